@@ -1,0 +1,39 @@
+"""The synthetic input generator: points lie in the open simplex, are
+reproducible from the seed, and follow Dirichlet(1, ..., 1) (each coordinate's
+marginal is Beta(1, m-1), with CDF 1 - (1 - t)^(m-1))."""
+import numpy as np
+from scipy import stats
+
+from paper_2202_00517_gb300.datagen import dirichlet_points, instance_mix
+
+
+def test_points_on_simplex_and_reproducible():
+    p = dirichlet_points(5000, 21, 1, np.float64)
+    assert p.shape == (5000, 21)
+    assert np.all(p > 0) and np.all(p < 1)
+    assert np.allclose(p.sum(1), 1.0, atol=1e-14)
+    assert np.array_equal(p, dirichlet_points(5000, 21, 1, np.float64))
+    assert not np.array_equal(p, dirichlet_points(5000, 21, 2, np.float64))
+    p32 = dirichlet_points(5000, 21, 1, np.float32)
+    assert p32.dtype == np.float32 and np.array_equal(p32, p.astype(np.float32))
+    # chunking does not change the values
+    assert np.array_equal(p, dirichlet_points(5000, 21, 1, np.float64, chunk=777))
+
+
+def test_dirichlet_marginals():
+    m = 6
+    p = dirichlet_points(20000, m, 4, np.float64)
+    for i in (0, 3, 5):
+        assert stats.kstest(p[:, i], lambda t: 1 - (1 - t) ** (m - 1)).pvalue > 1e-4
+
+
+def test_instance_mix():
+    mix = instance_mix(4096, 5)
+    ns = np.array([a for a, _, _ in mix])
+    assert ns.min() >= 200 and ns.max() <= 50000
+    assert {b for _, b, _ in mix} == {6, 11, 21}
+    assert {c for _, _, c in mix} == {8, 16, 32}
+    # log-uniform: log(n/200)/log(250) is close to uniform
+    u = np.log(ns / 200) / np.log(250)
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    assert mix == instance_mix(4096, 5)

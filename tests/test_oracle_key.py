@@ -1,0 +1,89 @@
+"""Pins of the oracle's KL comparator key (Sec. 2.2): key(x, y) = D(x||y).
+
+Each check ties the oracle to something outside itself: hand-worked closed forms,
+scipy's elementwise relative entropy, the closed form for a uniform y, and the
+exact zero of D(x||x).  A transposed operand (D(y||x)), a dropped -H(x) term or
+a sign error fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy.special import rel_entr
+
+import oracle
+from paper_2202_00517_gb300.datagen import dirichlet_points
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "kl_worked_example.txt")
+
+
+def _read_golden():
+    rows = []
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        xs, ys, _form, val = [s.strip() for s in line.split(";")]
+        rows.append((np.array([float(t) for t in xs.split(",")]),
+                     np.array([float(t) for t in ys.split(",")]), float(val)))
+    return rows
+
+
+def test_worked_examples():
+    for x, y, val in _read_golden():
+        k = oracle.keys_pairs(np.stack([x, y]), [0], [1])[0]
+        assert abs(k - val) <= 4e-16 * max(1.0, abs(val)) * 8, (x, y, k, val)
+
+
+def test_direction_is_x_first():
+    # D(x||y) != D(y||x) in the worked examples: the key must weight by x.
+    x, y, val = _read_golden()[0]
+    k_xy = oracle.keys_pairs(np.stack([x, y]), [0], [1])[0]
+    k_yx = oracle.keys_pairs(np.stack([x, y]), [1], [0])[0]
+    assert abs(k_xy - val) < 1e-15
+    assert abs(k_yx - val) > 1e-3
+
+
+def test_self_key_is_exactly_zero():
+    p = dirichlet_points(300, 7, 11, np.float64)
+    xs = np.arange(300)
+    k = oracle.keys_pairs(p, xs, xs)
+    assert np.all(k == 0.0)
+
+
+def test_matches_scipy_relative_entropy():
+    p = dirichlet_points(400, 21, 5, np.float64)
+    rng = np.random.default_rng(0)
+    xs = rng.integers(0, 400, 5000)
+    ys = rng.integers(0, 400, 5000)
+    k = oracle.keys_pairs(p, xs, ys)
+    ref = rel_entr(p[xs], p[ys]).sum(axis=1)
+    # scale of the terms: |negH(x)| + sum_i x_i |log y_i|
+    scale = np.abs((p[xs] * np.log(p[xs])).sum(1)) + (p[xs] * np.abs(np.log(p[ys]))).sum(1)
+    assert np.all(np.abs(k - ref) <= 1e-13 * scale)
+
+
+def test_uniform_y_closed_form():
+    # y uniform: D(x||u) = sum_i x_i log x_i + log(m) sum_i x_i
+    m = 9
+    p = dirichlet_points(50, m, 3, np.float64)
+    u = np.full((1, m), 1.0 / m)
+    pts = np.concatenate([p, u])
+    k = oracle.keys_pairs(pts, np.arange(50), np.full(50, 50))
+    ref = (p * np.log(p)).sum(1) + np.log(m) * p.sum(1)
+    assert np.allclose(k, ref, rtol=0, atol=1e-14)
+
+
+def test_gibbs_nonnegative():
+    p = dirichlet_points(200, 5, 2, np.float64)
+    rng = np.random.default_rng(1)
+    xs = rng.integers(0, 200, 3000)
+    ys = rng.integers(0, 200, 3000)
+    k = oracle.keys_pairs(p, xs, ys)
+    assert np.all(k >= -1e-14)
+
+
+def test_logs_table():
+    p = dirichlet_points(100, 6, 9, np.float64)
+    L, negH = oracle.logs(p)
+    assert np.array_equal(L, np.log(p))
+    assert np.allclose(negH, (p * np.log(p)).sum(1), rtol=1e-14, atol=0)

@@ -1,0 +1,76 @@
+"""The oracle's full build against what the paper prints and predicts.
+
+* Table 3 (Sec. 4.4): at n = 2e4 on the 9-simplex the statistical stop is reached
+  within 2 ceil(log_K n) rounds and the final friend clustering rate lies near the
+  printed value (tolerance: the paper's own spread across n and K plus sampling
+  noise of the rate, +-0.05).
+* Sec. 3.2 / Sec. 4.3: the number of rounds does not exceed twice the diameter of
+  the undirected initial graph (diameter by BFS).
+* Sec. 3.3 (iii): the clustering rate starts near zero (2K/n for a random K-out
+  graph) and rises before it plateaus.
+* Sec. 4.4 item 4: recall of the true K nearest neighbours is high at 10
+  coordinates ("95% or better"); checked here as >= 0.9 on 200 sampled points.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_00517_gb300.datagen import dirichlet_points
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_table3.txt")
+
+
+def _table3():
+    rows = []
+    for line in open(GOLD):
+        if line.startswith("#") or not line.strip():
+            continue
+        n, K, rounds, bound, fcc = line.split()
+        rows.append((int(n), int(K), int(rounds), int(bound), float(fcc)))
+    return rows
+
+
+def _recall(p, res, K, nq=200):
+    n = p.shape[0]
+    q = np.linspace(0, n - 1, nq).astype(np.int32)
+    bi, _ = oracle.bruteforce(p, K, q)
+    return float(np.mean([len(set(bi[t]) & set(res["idx"][x])) / K for t, x in enumerate(q)]))
+
+
+def test_table3_bound_is_as_printed():
+    for n, K, _rounds, bound, _fcc in _table3():
+        assert 2 * math.ceil(math.log(n) / math.log(K)) == bound
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("K", [16, 32])
+def test_table3_small_n(K):
+    row = [r for r in _table3() if r[0] == 20000 and r[1] == K][0]
+    n, _, _, bound, fcc_paper = row
+    p = dirichlet_points(n, 10, 7, np.float64)
+    res = oracle.build(p, K, 7, S=10000)
+    assert res["rounds"] <= bound
+    final = res["hits"][-1] / 10000
+    assert abs(final - fcc_paper) < 0.05, (final, fcc_paper)
+    assert res["hits"][0] / 10000 < 4 * 2 * K / n
+    assert _recall(p, res, K) >= 0.9
+
+
+def test_config1_rounds_within_twice_diameter():
+    n, m, K, seed = 2000, 6, 10, 0
+    p = dirichlet_points(n, m, seed, np.float64)
+    idx0, _ = oracle.init_graph(p, K, seed)
+    diam = oracle.diameter_exact(idx0)
+    assert diam > 0
+    res = oracle.build(p, K, seed)
+    assert res["rounds"] <= 2 * diam
+    h = res["hits"]
+    # the clustering rate starts near 2K/n and increases until the stop round
+    assert h[0] < 3 * 2 * K * 10000 / n
+    assert np.all(np.diff(h[:-1]) > 0)
+    assert h[-1] <= h[-2]
+    assert np.array_equal(res["idx"], oracle.build(p, K, seed)["idx"])
+    assert _recall(p, res, K) >= 0.9
