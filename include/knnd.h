@@ -1,0 +1,214 @@
+/*
+ * knnd.h -- C ABI of the GB300 (sm_103a) K-nearest-neighbour descent library
+ * for the Kullback-Leibler comparator on points of the probability simplex.
+ *
+ * Method: Baron & Darling, "Empirical complexity of comparator-based nearest
+ * neighbor descent", arXiv:2202.00517.
+ *   - problem statement (Sec. 2.1, Sec. 2.3): a set S of n objects and, for
+ *     each x, a total order on S \ {x}; the output is the K-out digraph from
+ *     each x to its K most similar objects;
+ *   - comparator (Sec. 2.2, Sec. 4.4): y precedes z for x when
+ *     D(x||y) < D(x||z), D(x||y) = sum_i x_i log(x_i / y_i); ties are broken
+ *     by the smaller index;
+ *   - initial graph (Sec. 3.2): every x picks K distinct friends uniformly;
+ *   - one round (Sec. 3.1, Sec. 4.2): every x meets its co-friends, its
+ *     friends' friends and its co-friends' friends; its new friend list is the
+ *     K best of those and its old friends; all lists change together;
+ *   - termination (Sec. 3.3): a sampled friend clustering rate; stop at the
+ *     first round at which it does not increase.
+ *
+ * Conventions shared by every call:
+ *   - Points: n rows of m coordinates, row-major with a leading dimension of
+ *     `ld` elements (ld >= m), KNND_F32 or KNND_F64.  Every coordinate must be
+ *     finite and > 0 (points need not sum to exactly 1; they are used as
+ *     stored).  Point pointers are DEVICE pointers unless a name says _host.
+ *   - Graph: idx is n x K int32 (row x = x's friends), key is n x K float64
+ *     (key[x][t] = D(x || idx[x][t]) evaluated in FP64 as
+ *     sum_i x_i log x_i - sum_i x_i log y_i), newflag is n x K uint8 (1 when
+ *     the entry was not in the row before the call).  Each row is sorted by
+ *     (key ascending, idx ascending).  Caller-owned device buffers.
+ *   - Work is enqueued on the handle's stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).  Calls that return a host
+ *     value synchronise that stream; the others are stream-ordered.
+ *   - Scratch memory lives in the handle: it is allocated by knnd_create and
+ *     released by knnd_destroy.  Calls on one handle must not overlap.
+ *   - Every call returns a knnd_status.  Arguments are validated on the host
+ *     before any launch; on an error nothing is enqueued unless stated.
+ *     No C++ exception crosses this interface.
+ */
+#ifndef KNND_H
+#define KNND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t knnd_status;
+#define KNND_OK 0
+#define KNND_EINVAL (-1)    /* bad argument: null pointer, shape or parameter out of range */
+#define KNND_EDOMAIN (-2)   /* a coordinate is not finite or not > 0 (found on the device) */
+#define KNND_ENOMEM (-3)    /* device allocation failed */
+#define KNND_ECUDA (-4)     /* a CUDA runtime call or kernel launch failed */
+#define KNND_ETIMEOUT (-5)  /* a bounded device wait ran out */
+#define KNND_EOVERFLOW (-6) /* a size exceeds an internal limit */
+#define KNND_ESTATE (-7)    /* call out of order (e.g. round before any prepare) */
+
+typedef int32_t knnd_dtype;
+#define KNND_F32 0
+#define KNND_F64 1
+
+/* How the join scores candidate pairs.  Every form returns the same graph:
+ * the mixed forms filter with a rigorous FP32 error bound and re-score in
+ * FP64 every candidate the bound cannot decide. */
+typedef int32_t knnd_precision;
+#define KNND_PREC_FP64 0        /* every pair scored in FP64 */
+#define KNND_PREC_MIXED_FP32 1  /* FP32 CUDA-core filter + FP64 re-score */
+#define KNND_PREC_AUTO 3        /* the library chooses (currently MIXED_FP32) */
+
+#define KNND_MAX_K 64
+#define KNND_MAX_M 128
+#define KNND_MAX_ROUNDS 64
+
+/* Termination and debugging parameters (NULL -> the defaults shown). */
+typedef struct {
+    int32_t fcc_samples;          /* S, samples of the clustering rate per round (10000) */
+    int32_t max_rounds;           /* cap on rounds, 1..KNND_MAX_ROUNDS (64) */
+    int32_t stop_on_zero_updates; /* also stop after a round with no update (1) */
+    int32_t debug;                /* 1: device bounds checks and error-bound audit (0) */
+    int32_t timing;               /* 1: CUDA events around every phase, see knnd_stats (0) */
+} knnd_params;
+
+/* Why knnd_build stopped. */
+#define KNND_STOP_FCC 1        /* clustering hits did not increase (Sec. 3.3 (iv)) */
+#define KNND_STOP_ZERO 2       /* a round made no update */
+#define KNND_STOP_MAX_ROUNDS 3 /* max_rounds reached */
+
+/* Per-build report, filled by knnd_build / knnd_build_host (host memory). */
+typedef struct {
+    int32_t rounds;                          /* rounds performed, the stopping one included */
+    int32_t stop_reason;                     /* KNND_STOP_* */
+    int64_t updates[KNND_MAX_ROUNDS];        /* updates[r-1]: new list entries made by round r */
+    int64_t fcc_hits[KNND_MAX_ROUNDS + 1];   /* fcc_hits[r]: hits of the graph after round r */
+    int64_t proposals;                       /* candidate pairs scored by the join, all rounds */
+    int64_t init_pairs;                      /* pairs scored by the initial graph (n*K) */
+    int64_t rescored;                        /* mixed forms: pairs re-scored in FP64 */
+    int64_t bound_violations;                /* debug audit: FP32 errors above the bound (must be 0) */
+} knnd_build_info;
+
+/* Phases of the descent, for the per-phase timing of knnd_stats. */
+#define KNND_PHASE_PREPARE 0 /* log table, -H(x), FP32 copies */
+#define KNND_PHASE_INIT 1    /* initial random K-out graph */
+#define KNND_PHASE_CSR 2     /* co-friend lists (count, scan, fill) */
+#define KNND_PHASE_JOIN 3    /* hub-centric local join */
+#define KNND_PHASE_MERGE 4   /* bounded top-K update, update count */
+#define KNND_PHASE_FCC 5     /* clustering-rate sample */
+#define KNND_NUM_PHASES 6
+
+/* Counters kept by a handle since its creation. */
+typedef struct {
+    int64_t kernel_launches;                  /* kernels this handle has launched */
+    int64_t rounds;                           /* rounds run */
+    int64_t workspace_bytes;                  /* device scratch held by the handle */
+    int64_t phase_count[KNND_NUM_PHASES];     /* timed instances of each phase (timing = 1) */
+    double phase_ms[KNND_NUM_PHASES];         /* their summed CUDA-event milliseconds */
+} knnd_stats;
+
+typedef struct knnd_handle knnd_handle;
+
+/* Create a handle for n points of m coordinates and K friends per point
+ * (2 <= K <= min(n-1, KNND_MAX_K), 1 <= m <= KNND_MAX_M, n < 2^31) and
+ * allocate its scratch on the current CUDA device.  `stream` is the
+ * cudaStream_t (as void*) all later calls enqueue on.
+ * Errors: EINVAL (shape or parameter out of range, out == NULL), ENOMEM,
+ * ECUDA.  On error *out is NULL. */
+knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd_dtype dtype,
+                        knnd_precision precision, const knnd_params *params, void *stream);
+
+/* Release the handle and its scratch (synchronises its stream).  NULL is a no-op. */
+void knnd_destroy(knnd_handle *h);
+
+/* Replace the stream later calls enqueue on. */
+knnd_status knnd_set_stream(knnd_handle *h, void *stream);
+
+/* Precompute from the points (log table, -H(x), FP32 copies and the FP32
+ * error-bound scale).  Reads n x m coordinates at `points` (device, row
+ * stride ld elements).  Synchronises the stream to report EDOMAIN when a
+ * coordinate is not finite or not > 0.  knnd_init_graph, knnd_round and
+ * knnd_build call it themselves when given a non-NULL points pointer. */
+knnd_status knnd_prepare(knnd_handle *h, const void *points, int64_t ld);
+
+/* Initial random K-out graph (Sec. 3.2): every x draws K distinct friends
+ * y != x from the Philox4x32-10 stream keyed by `seed` with counter
+ * (x, 0, 0, block), each as y' = Lemire-uniform in [0, n-1), y = y' + (y' >= x),
+ * a repeated value drawn again; rows are then sorted by (key, idx).
+ * points: device points or NULL (reuse the prepared ones).
+ * idx, key: out, n x K device.  newflag: out, n x K device or NULL (all 1).
+ * Errors: EINVAL, ESTATE (points NULL and never prepared), EDOMAIN, ECUDA. */
+knnd_status knnd_init_graph(knnd_handle *h, const void *points, int64_t ld, uint64_t seed, int32_t *idx,
+                            double *key, uint8_t *newflag);
+
+/* One synchronous round r >= 1 (Sec. 3.1, Sec. 4.2) from G_{r-1} to G_r, in
+ * place: idx/key hold G_{r-1} on entry and G_r on return (device, n x K,
+ * rows sorted by (key, idx)); newflag (device n x K or NULL) marks the
+ * entries of G_r absent from G_{r-1}.  Pool of x: friends, co-friends,
+ * friends of friends, friends of co-friends, minus x; G_r(x) = its K best.
+ * updates (device int64 or NULL) receives the number of new entries;
+ * fcc_hits (device int64 or NULL) receives the clustering hits of G_r drawn
+ * from stream (seed, counter (s, r, 1, block)) for s < fcc_samples
+ * (Sec. 3.3).  points: device points or NULL (reuse the prepared ones).
+ * Errors: EINVAL, ESTATE, EDOMAIN, ECUDA, EOVERFLOW (debug checks). */
+knnd_status knnd_round(knnd_handle *h, const void *points, int64_t ld, uint64_t seed, int32_t round,
+                       int32_t *idx, double *key, uint8_t *newflag, int64_t *updates, int64_t *fcc_hits);
+
+/* Clustering hits (Sec. 3.3) of graph idx (device n x K) for round number
+ * `round`: S samples drawn from stream (seed, counter (s, round, 1, block)):
+ * x = uniform [0, n), i = uniform [0, K), j' = uniform [0, K-1),
+ * j = j' + (j' >= i); a hit when idx[x][j] is a friend of idx[x][i] or the
+ * reverse.  hits: device int64, overwritten.  Errors: EINVAL, ECUDA. */
+knnd_status knnd_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits);
+
+/* Full build (Sec. 3): initial graph, then rounds until the clustering hits
+ * of round r do not exceed those of round r-1, or (stop_on_zero_updates) a
+ * round makes no update, or max_rounds.  points: device (non-NULL).
+ * idx, key: out, device n x K (G after the stopping round).  newflag:
+ * device n x K or NULL.  info: host, filled.  Synchronises the stream once
+ * per round to read the stop decision.
+ * Errors: EINVAL, EDOMAIN, ECUDA, EOVERFLOW. */
+knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t seed, int32_t *idx,
+                       double *key, uint8_t *newflag, knnd_build_info *info);
+
+/* knnd_build from and to HOST memory: copies the points in (one
+ * cudaMemcpyAsync into handle-owned device memory), builds, and copies idx
+ * and key out; returns after the copies complete.  points_host: n x m with
+ * row stride ld; idx_host (n x K int32), key_host (n x K float64): host
+ * outputs (pinned memory gives full copy bandwidth).  Errors: as knnd_build. */
+knnd_status knnd_build_host(knnd_handle *h, const void *points_host, int64_t ld, uint64_t seed,
+                            int32_t *idx_host, double *key_host, knnd_build_info *info);
+
+/* Synchronise the handle's stream and return (and clear) the sticky device
+ * status: EDOMAIN (bad coordinate), EINVAL (a graph index outside [0, n)
+ * met by a kernel, which skipped it), EOVERFLOW (debug bucket check), or OK.
+ * Kernels never access memory out of bounds on bad input; they record it
+ * here instead. */
+knnd_status knnd_sync(knnd_handle *h);
+
+/* Counters of the handle (host struct).  Synchronises the stream when
+ * timing is on, to read the pending phase events. */
+knnd_status knnd_get_stats(knnd_handle *h, knnd_stats *stats);
+
+/* Zero the phase timings and launch counters of knnd_stats. */
+knnd_status knnd_reset_stats(knnd_handle *h);
+
+/* Static text for a status code. */
+const char *knnd_status_string(knnd_status s);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t knnd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNND_H */

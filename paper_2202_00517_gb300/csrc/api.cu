@@ -1,0 +1,449 @@
+// api.cu -- the C ABI of include/knnd.h: handle, scratch, argument checks and
+// the launch sequences of init, round and build.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "knnd_internal.cuh"
+
+using namespace knnd;
+
+namespace {
+
+constexpr int32_t kVersion = 100;  // 0.1.0
+
+knnd_params default_params()
+{
+    knnd_params p;
+    p.fcc_samples = 10000;
+    p.max_rounds = KNND_MAX_ROUNDS;
+    p.stop_on_zero_updates = 1;
+    p.debug = 0;
+    p.timing = 0;
+    return p;
+}
+
+knnd_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return KNND_OK;
+    if (e == cudaErrorMemoryAllocation) return KNND_ENOMEM;
+    return KNND_ECUDA;
+}
+
+template <typename T>
+knnd_status dalloc(knnd_handle *h, T **p, int64_t count)
+{
+    *p = nullptr;
+    if (count <= 0) return KNND_OK;
+    const size_t bytes = sizeof(T) * (size_t)count;
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return KNND_ENOMEM;
+    }
+    h->ws_bytes += (int64_t)bytes;
+    return KNND_OK;
+}
+
+void free_all(knnd_handle *h)
+{
+    void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg,
+                    h->cof_off, h->cof, h->scan_tmp, h->tau, h->idxK, h->phi, h->Ex, h->bcnt, h->bkey,
+                    h->bidx, h->bent, h->cnt, h->pts_dev, h->idx_dev, h->key_dev};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->cnt_host) cudaFreeHost(h->cnt_host);
+    if (h->events_made)
+        for (int i = 0; i < 2 * knnd_handle::kMaxPending; ++i)
+            if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+}
+
+// Reads and clears the sticky device error word (synchronises the stream).
+knnd_status take_device_error(knnd_handle *h)
+{
+    int32_t e = 0;
+    cudaError_t c = cudaMemcpyAsync(&e, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (c == cudaSuccess) c = cudaStreamSynchronize(h->stream);
+    if (c != cudaSuccess) return cuda_status(c);
+    if (e == 0) return KNND_OK;
+    cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream);
+    cudaStreamSynchronize(h->stream);
+    if (e & kErrDomain) return KNND_EDOMAIN;
+    if (e & kErrIndex) return KNND_EINVAL;
+    return KNND_EOVERFLOW;
+}
+
+// ---- per-phase CUDA-event timing --------------------------------------------
+void resolve_phases(knnd_handle *h)
+{
+    if (h->npend == 0) return;
+    cudaEventSynchronize(h->ev[2 * (h->npend - 1) + 1]);
+    for (int i = 0; i < h->npend; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess) {
+            h->phase_ms[h->pend_phase[i]] += ms;
+            h->phase_count[h->pend_phase[i]] += 1;
+        }
+    }
+    h->npend = 0;
+}
+
+int phase_begin(knnd_handle *h)
+{
+    if (!h->events_made) return -1;
+    if (h->npend == knnd_handle::kMaxPending) resolve_phases(h);
+    const int slot = h->npend;
+    cudaEventRecord(h->ev[2 * slot], h->stream);
+    return slot;
+}
+
+void phase_end(knnd_handle *h, int slot, int phase)
+{
+    if (slot < 0) return;
+    cudaEventRecord(h->ev[2 * slot + 1], h->stream);
+    h->pend_phase[slot] = phase;
+    h->npend += 1;
+}
+
+knnd_status check_points(const knnd_handle *h, const void *points, int64_t ld)
+{
+    if (!points) return KNND_EINVAL;
+    if (ld < h->m) return KNND_EINVAL;
+    return KNND_OK;
+}
+
+knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
+{
+    knnd_status s = check_points(h, points, ld);
+    if (s) return s;
+    const int t = phase_begin(h);
+    cudaError_t e = launch_precompute(h, points, ld);
+    phase_end(h, t, KNND_PHASE_PREPARE);
+    if (e != cudaSuccess) return cuda_status(e);
+    s = take_device_error(h);
+    h->prepared = (s == KNND_OK);
+    return s;
+}
+
+// G_{r-1} -> G_r in place; counters kCntUpdates/kCntRescored accumulate.
+knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx, double *key, uint8_t *newflag,
+                     int64_t *fcc_hits)
+{
+    int t = phase_begin(h);
+    cudaError_t e = launch_reverse_csr(h, idx, key);
+    phase_end(h, t, KNND_PHASE_CSR);
+    if (e == cudaSuccess) {
+        t = phase_begin(h);
+        e = launch_join(h, idx);
+        phase_end(h, t, KNND_PHASE_JOIN);
+    }
+    if (e == cudaSuccess) {
+        t = phase_begin(h);
+        e = launch_merge(h, idx, key, newflag);
+        phase_end(h, t, KNND_PHASE_MERGE);
+    }
+    if (e == cudaSuccess && fcc_hits) {
+        t = phase_begin(h);
+        e = launch_fcc(h, idx, seed, round, fcc_hits);
+        phase_end(h, t, KNND_PHASE_FCC);
+    }
+    h->rounds_run += 1;
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *knnd_status_string(knnd_status s)
+{
+    switch (s) {
+    case KNND_OK: return "ok";
+    case KNND_EINVAL: return "invalid argument";
+    case KNND_EDOMAIN: return "a coordinate is not finite or not > 0";
+    case KNND_ENOMEM: return "device allocation failed";
+    case KNND_ECUDA: return "CUDA error";
+    case KNND_ETIMEOUT: return "bounded device wait ran out";
+    case KNND_EOVERFLOW: return "size exceeds an internal limit";
+    case KNND_ESTATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+int32_t knnd_version(void) { return kVersion; }
+
+knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd_dtype dtype,
+                        knnd_precision precision, const knnd_params *params, void *stream)
+{
+    if (!out) return KNND_EINVAL;
+    *out = nullptr;
+    if (n < 3 || n >= ((int64_t)1 << 31)) return KNND_EINVAL;
+    if (m < 1 || m > KNND_MAX_M) return KNND_EINVAL;
+    if (K < 2 || K > KNND_MAX_K || (int64_t)K >= n) return KNND_EINVAL;
+    if (dtype != KNND_F32 && dtype != KNND_F64) return KNND_EINVAL;
+    if (precision == KNND_PREC_AUTO) precision = KNND_PREC_MIXED_FP32;
+    if (precision != KNND_PREC_FP64 && precision != KNND_PREC_MIXED_FP32) return KNND_EINVAL;
+    knnd_params prm = params ? *params : default_params();
+    if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
+    // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
+    if ((int64_t)K * K + (int64_t)(K + 1) * (n - 1) >= ((int64_t)1 << 31)) return KNND_EOVERFLOW;
+
+    knnd_handle *h = new (std::nothrow) knnd_handle;
+    if (!h) return KNND_ENOMEM;
+    std::memset((void *)h, 0, sizeof(*h));
+    h->n = n;
+    h->m = m;
+    h->MP = pad_coords(m);
+    h->K = K;
+    h->dtype = dtype;
+    h->prec = precision;
+    h->prm = prm;
+    h->stream = (cudaStream_t)stream;
+    // c_m of |fp32 dot - fp64 dot| <= c_m sum_i |x_i log y_i|: m FP32 fma roundings,
+    // the FP32 rounding of log y_i and of x_i, doubled-rounding slack; 1% headroom.
+    h->bound_c = (double)(m + 6) * 0x1p-24 * 1.01;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return KNND_ECUDA;
+    }
+    const int64_t MP = h->MP, nK = n * K;
+    knnd_status s = KNND_OK;
+    const int64_t ntiles = (n + 2047) / 2048;
+    h->scan_tmp_len = ntiles;
+    const bool mixed = precision != KNND_PREC_FP64;
+    h->bucket_cap = nK * (2 * (int64_t)K + 1);
+    if (!s) s = dalloc(h, &h->X64, n * MP);
+    if (!s) s = dalloc(h, &h->L64, n * MP);
+    if (!s) s = dalloc(h, &h->X32, n * MP);
+    if (!s) s = dalloc(h, &h->L32, n * MP);
+    if (!s) s = dalloc(h, &h->negH, n);
+    if (!s) s = dalloc(h, &h->nx, n);
+    if (!s) s = dalloc(h, &h->smax_bits, 1);
+    if (!s) s = dalloc(h, &h->err, 1);
+    if (!s) s = dalloc(h, &h->deg, n);
+    if (!s) s = dalloc(h, &h->cof_off, n + 1);
+    if (!s) s = dalloc(h, &h->cof, nK);
+    if (!s) s = dalloc(h, &h->scan_tmp, ntiles);
+    if (!s) s = dalloc(h, &h->tau, n);
+    if (!s) s = dalloc(h, &h->idxK, n);
+    if (!s) s = dalloc(h, &h->phi, n);
+    if (!s) s = dalloc(h, &h->Ex, n);
+    if (!s) s = dalloc(h, &h->bcnt, n);
+    if (!s && mixed) s = dalloc(h, &h->bent, h->bucket_cap);
+    if (!s && !mixed) s = dalloc(h, &h->bkey, h->bucket_cap);
+    if (!s && !mixed) s = dalloc(h, &h->bidx, h->bucket_cap);
+    if (!s) s = dalloc(h, &h->cnt, kCntNum);
+    if (!s && cudaMallocHost((void **)&h->cnt_host, sizeof(int64_t) * kCntNum) != cudaSuccess) s = KNND_ENOMEM;
+    if (!s && prm.timing) {
+        for (int i = 0; i < 2 * knnd_handle::kMaxPending && !s; ++i)
+            if (cudaEventCreate(&h->ev[i]) != cudaSuccess) s = KNND_ECUDA;
+        h->events_made = true;
+    }
+    if (!s) {
+        cudaError_t e = cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->cnt, 0, sizeof(int64_t) * kCntNum, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        s = cuda_status(e);
+    }
+    if (s) {
+        free_all(h);
+        delete h;
+        (void)cudaGetLastError();
+        return s;
+    }
+    *out = h;
+    return KNND_OK;
+}
+
+void knnd_destroy(knnd_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+knnd_status knnd_set_stream(knnd_handle *h, void *stream)
+{
+    if (!h) return KNND_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return KNND_OK;
+}
+
+knnd_status knnd_prepare(knnd_handle *h, const void *points, int64_t ld)
+{
+    if (!h) return KNND_EINVAL;
+    return do_prepare(h, points, ld);
+}
+
+knnd_status knnd_init_graph(knnd_handle *h, const void *points, int64_t ld, uint64_t seed, int32_t *idx,
+                            double *key, uint8_t *newflag)
+{
+    if (!h || !idx || !key) return KNND_EINVAL;
+    if (points) {
+        knnd_status s = do_prepare(h, points, ld);
+        if (s) return s;
+    } else if (!h->prepared) {
+        return KNND_ESTATE;
+    }
+    const int t = phase_begin(h);
+    cudaError_t e = launch_init_graph(h, seed, idx, key, newflag);
+    phase_end(h, t, KNND_PHASE_INIT);
+    return cuda_status(e);
+}
+
+knnd_status knnd_round(knnd_handle *h, const void *points, int64_t ld, uint64_t seed, int32_t round,
+                       int32_t *idx, double *key, uint8_t *newflag, int64_t *updates, int64_t *fcc_hits)
+{
+    if (!h || !idx || !key || round < 1) return KNND_EINVAL;
+    if (points) {
+        knnd_status s = do_prepare(h, points, ld);
+        if (s) return s;
+    } else if (!h->prepared) {
+        return KNND_ESTATE;
+    }
+    cudaError_t e = cudaMemsetAsync(h->cnt, 0, sizeof(int64_t) * kCntNum, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    knnd_status s = do_round(h, seed, round, idx, key, newflag, fcc_hits ? fcc_hits : nullptr);
+    if (s) return s;
+    if (updates) {
+        e = cudaMemcpyAsync(updates, h->cnt + kCntUpdates, sizeof(int64_t), cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return KNND_OK;
+}
+
+knnd_status knnd_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits)
+{
+    if (!h || !idx || !hits || round < 0) return KNND_EINVAL;
+    return cuda_status(launch_fcc(h, idx, seed, round, hits));
+}
+
+knnd_status knnd_sync(knnd_handle *h)
+{
+    if (!h) return KNND_EINVAL;
+    return take_device_error(h);
+}
+
+knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t seed, int32_t *idx, double *key,
+                       uint8_t *newflag, knnd_build_info *info)
+{
+    if (!h || !points || !idx || !key || !info) return KNND_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    knnd_status s = do_prepare(h, points, ld);
+    if (s) return s;
+    int t = phase_begin(h);
+    cudaError_t e = launch_init_graph(h, seed, idx, key, newflag);
+    phase_end(h, t, KNND_PHASE_INIT);
+    if (e != cudaSuccess) return cuda_status(e);
+    int64_t *d = h->cnt;
+    int64_t *hst = h->cnt_host;
+    e = cudaMemsetAsync(d, 0, sizeof(int64_t) * kCntNum, h->stream);
+    if (e == cudaSuccess) {
+        t = phase_begin(h);
+        e = launch_fcc(h, idx, seed, 0, d + kCntHits);
+        phase_end(h, t, KNND_PHASE_FCC);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hst, d, sizeof(int64_t) * kCntNum, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    info->fcc_hits[0] = hst[kCntHits];
+    info->init_pairs = h->n * h->K;
+    const int64_t per_round = h->n * (int64_t)h->K * (2 * (int64_t)h->K + 1);
+    int32_t r = 0;
+    while (r < h->prm.max_rounds) {
+        r += 1;
+        e = cudaMemsetAsync(d, 0, sizeof(int64_t) * kCntNum, h->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        s = do_round(h, seed, r, idx, key, newflag, d + kCntHits);
+        if (s) return s;
+        e = cudaMemcpyAsync(hst, d, sizeof(int64_t) * kCntNum, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        info->updates[r - 1] = hst[kCntUpdates];
+        info->fcc_hits[r] = hst[kCntHits];
+        info->rescored += hst[kCntRescored];
+        info->bound_violations += hst[kCntBoundViol];
+        info->proposals += per_round;
+        info->rounds = r;
+        if (info->fcc_hits[r] <= info->fcc_hits[r - 1]) {
+            info->stop_reason = KNND_STOP_FCC;
+            break;
+        }
+        if (h->prm.stop_on_zero_updates && info->updates[r - 1] == 0) {
+            info->stop_reason = KNND_STOP_ZERO;
+            break;
+        }
+    }
+    if (!info->stop_reason) info->stop_reason = KNND_STOP_MAX_ROUNDS;
+    return take_device_error(h);
+}
+
+knnd_status knnd_build_host(knnd_handle *h, const void *points_host, int64_t ld, uint64_t seed, int32_t *idx_host,
+                            double *key_host, knnd_build_info *info)
+{
+    if (!h || !points_host || !idx_host || !key_host || !info) return KNND_EINVAL;
+    if (ld < h->m) return KNND_EINVAL;
+    const size_t esz = h->dtype == KNND_F32 ? 4 : 8;
+    const int64_t pbytes = (int64_t)esz * ((h->n - 1) * ld + h->m);
+    const int64_t nK = h->n * h->K;
+    if (!h->pts_dev || h->pts_dev_bytes < pbytes) {
+        if (h->pts_dev) {
+            cudaFree(h->pts_dev);
+            h->ws_bytes -= h->pts_dev_bytes;
+            h->pts_dev = nullptr;
+        }
+        if (cudaMalloc(&h->pts_dev, (size_t)pbytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return KNND_ENOMEM;
+        }
+        h->pts_dev_bytes = pbytes;
+        h->ws_bytes += pbytes;
+    }
+    if (!h->idx_dev) {
+        knnd_status s = dalloc(h, &h->idx_dev, nK);
+        if (!s) s = dalloc(h, &h->key_dev, nK);
+        if (s) return s;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->pts_dev, points_host, (size_t)pbytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    knnd_status s = knnd_build(h, h->pts_dev, ld, seed, h->idx_dev, h->key_dev, nullptr, info);
+    if (s) return s;
+    e = cudaMemcpyAsync(idx_host, h->idx_dev, sizeof(int32_t) * nK, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(key_host, h->key_dev, sizeof(double) * nK, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+knnd_status knnd_get_stats(knnd_handle *h, knnd_stats *st)
+{
+    if (!h || !st) return KNND_EINVAL;
+    resolve_phases(h);
+    st->kernel_launches = h->launches;
+    st->rounds = h->rounds_run;
+    st->workspace_bytes = h->ws_bytes;
+    for (int p = 0; p < KNND_NUM_PHASES; ++p) {
+        st->phase_count[p] = h->phase_count[p];
+        st->phase_ms[p] = h->phase_ms[p];
+    }
+    return KNND_OK;
+}
+
+knnd_status knnd_reset_stats(knnd_handle *h)
+{
+    if (!h) return KNND_EINVAL;
+    resolve_phases(h);
+    for (int p = 0; p < KNND_NUM_PHASES; ++p) {
+        h->phase_count[p] = 0;
+        h->phase_ms[p] = 0.0;
+    }
+    h->launches = 0;
+    h->rounds_run = 0;
+    return KNND_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// csr.cu -- co-friend lists (Sec. 3.1, Sec. 4.2: "coFriends is derived from
+// friends") as a CSR built per round: in-degree count, exclusive scan, fill.
+// The count pass also extracts each row's K-th entry, the threshold of the
+// join's filter, and (mixed form) the FP32 rejection threshold phi.
+#include "knnd_internal.cuh"
+
+namespace knnd {
+
+// One thread per arc e = x*K + t (x -> idx[e]).
+__global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *__restrict__ key, int64_t n, int K,
+                                 int32_t *__restrict__ deg, double *__restrict__ tau, int32_t *__restrict__ idxK,
+                                 const double *__restrict__ negH, const double *__restrict__ nx,
+                                 const unsigned long long *__restrict__ smax_bits, double bound_c,
+                                 float *__restrict__ phi, double *__restrict__ Ex, int32_t *err)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * K) return;
+    const int32_t v = idx[e];
+    if (v < 0 || v >= n) {
+        atomicOr(err, kErrIndex);
+    } else {
+        atomicAdd(&deg[v], 1);
+    }
+    if (e % K == K - 1) {
+        const int64_t x = e / K;
+        const double t = key[e];
+        tau[x] = t;
+        idxK[x] = v;
+        if (phi) {
+            // |fp32 dot - fp64 dot| <= c_m * sum_i |x_i||log y_i| <= c_m * nx(x) * max|log|.
+            // margin covers the FP64 roundings of the key and threshold arithmetic.
+            const double smax = __longlong_as_double((long long)*smax_bits);
+            const double nh = negH[x];
+            const double margin = 0x1p-40 * (fabs(nh) + nx[x] * smax + 1.0);
+            const double E = bound_c * nx[x] * smax + 0x1p-100 + margin;
+            Ex[x] = E;
+            phi[x] = __double2float_rd(nh - t - E);
+        }
+    }
+}
+
+// Exclusive scan of the int32 degrees into int64 offsets, in three passes over
+// tiles of kScanTile elements.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *total)
+{
+    __shared__ int64_t wsum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t s = (lane < kScanThreads / 32) ? wsum[lane] : 0;
+        int64_t si = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += t;
+        }
+        if (lane < kScanThreads / 32) wsum[lane] = si - s;
+        if (lane == kScanThreads / 32 - 1) *total = si;
+    }
+    __syncthreads();
+    int64_t r = incl - v + wsum[w];
+    __syncthreads();
+    return r;
+}
+
+__global__ void scan_tiles_kernel(const int32_t *__restrict__ deg, int64_t n, int64_t *__restrict__ tile_sum)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int64_t s = 0;
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < n) s += deg[base + i];
+    __shared__ int64_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void scan_sums_kernel(int64_t *__restrict__ tile_sum, int64_t ntiles, int64_t *__restrict__ off,
+                                 int64_t n)
+{
+    __shared__ int64_t tot;
+    int64_t carry = 0;
+    for (int64_t b = 0; b < ntiles; b += kScanThreads) {
+        const int64_t i = b + threadIdx.x;
+        const int64_t v = (i < ntiles) ? tile_sum[i] : 0;
+        const int64_t ex = block_exclusive_scan(v, &tot);
+        if (i < ntiles) tile_sum[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[n] = carry;
+}
+
+__global__ void scan_apply_kernel(const int32_t *__restrict__ deg, int64_t n, const int64_t *__restrict__ tile_off,
+                                  int64_t *__restrict__ off)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int64_t v[kScanPer];
+    int64_t s = 0;
+    for (int i = 0; i < kScanPer; ++i) {
+        v[i] = (base + i < n) ? deg[base + i] : 0;
+        s += v[i];
+    }
+    __shared__ int64_t tot;
+    int64_t run = block_exclusive_scan(s, &tot) + tile_off[blockIdx.x];
+    for (int i = 0; i < kScanPer; ++i) {
+        if (base + i < n) off[base + i] = run;
+        run += v[i];
+    }
+}
+
+// One thread per arc x -> v: append x to coF(v).  The order inside a list is
+// not fixed; every consumer treats the list as a set.
+__global__ void csr_fill_kernel(const int32_t *__restrict__ idx, int64_t n, int K, const int64_t *__restrict__ off,
+                                int32_t *__restrict__ cursor, int32_t *__restrict__ cof)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * K) return;
+    const int32_t v = idx[e];
+    if (v < 0 || v >= n) return;
+    const int32_t p = atomicAdd(&cursor[v], 1);
+    cof[off[v] + p] = (int32_t)(e / K);
+}
+
+cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key)
+{
+    const int64_t n = h->n;
+    const int K = h->K;
+    const int64_t E = n * K;
+    const int threads = 256;
+    const unsigned eblocks = (unsigned)((E + threads - 1) / threads);
+    cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
+    const bool mixed = h->prec != KNND_PREC_FP64;
+    csr_count_kernel<<<eblocks, threads, 0, h->stream>>>(idx, key, n, K, h->deg, h->tau, h->idxK, h->negH, h->nx,
+                                                         h->smax_bits, h->bound_c, mixed ? h->phi : nullptr,
+                                                         h->Ex, h->err);
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    scan_tiles_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp);
+    scan_sums_kernel<<<1, kScanThreads, 0, h->stream>>>(h->scan_tmp, ntiles, h->cof_off, n);
+    scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp, h->cof_off);
+    cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
+    csr_fill_kernel<<<eblocks, threads, 0, h->stream>>>(idx, n, K, h->cof_off, h->deg, h->cof);
+    h->launches += 5;
+    return cudaGetLastError();
+}
+
+}  // namespace knnd

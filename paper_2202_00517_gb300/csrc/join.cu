@@ -1,0 +1,456 @@
+// join.cu -- the local join of one round (Sec. 3.1 "Meet", Sec. 4.2
+// proposeNewFriendSet), organised around hubs.
+//
+// Every pair the pool of Sec. 3.1 contains is met at exactly one hub role:
+//   x in coF(v), y in F(v)   <=>  y is a friend of a friend of x
+//   x in F(v),   y in F(v)   <=>  y is a friend of a co-friend of x
+//   x in F(v),   y = v       <=>  y is a co-friend of x
+// so hub v's tile is rows R_v = F(v) + coF(v) against columns F(v), plus the
+// column v for the rows of F(v).  The tile is a small dense contraction of the
+// rows' coordinates with the columns' log table: key(x, y) = negH(x) - <x, L(y)>.
+//
+// One warp per hub.  Lane j holds column j's log row in registers; the rows
+// are staged 32 at a time in shared memory and broadcast.  A pair that can
+// still beat row x's current K-th entry is appended to x's bucket (capacity
+// K*K + (K+1)*indeg(x), so it cannot overflow): one atomicAdd per (hub, row)
+// reserves the row's slots, then the surviving lanes write consecutively.
+//
+// FP64 form: key in FP64, exact filter (key, y) < (tau_x, idxK_x).
+// Mixed form: FP32 dot with FP32 accumulation; the pair is rejected only when
+// dot + E_x < negH_x - tau_x, i.e. when it provably cannot beat the K-th
+// entry (phi_x = that threshold, rounded down); the merge re-scores in FP64.
+#include <algorithm>
+
+#include "knnd_internal.cuh"
+
+namespace knnd {
+
+struct JoinArgs {
+    int64_t n;
+    int K;
+    const int32_t *idx;
+    const int64_t *cof_off;
+    const int32_t *cof;
+    const float *X32;
+    const float *L32;
+    const double *X64;
+    const double *L64;
+    const double *negH;
+    const double *tau;
+    const int32_t *idxK;
+    const float *phi;
+    int32_t *bcnt;
+    int2 *bent;
+    double *bkey;
+    int32_t *bidx;
+    int32_t *err;
+    int debug;
+};
+
+__device__ __forceinline__ bool valid_id(int64_t v, int64_t n) { return v >= 0 && v < n; }
+
+// ------------------------------------------------------------------ mixed
+template <int MP, int CPL>
+struct MixedSmem {
+    static constexpr int RS = MP + 4;  // row stride in floats (16-byte aligned, conflict-free float4 phases)
+    static constexpr int X_FLOATS = 33 * RS;
+    static constexpr int D_FLOATS = CPL * 32 * 33;
+    static constexpr int WARP_FLOATS = X_FLOATS + D_FLOATS;
+};
+
+template <int MP, int CPL>
+__global__ void __launch_bounds__(256) join_mixed_kernel(JoinArgs a)
+{
+    using S = MixedSmem<MP, CPL>;
+    extern __shared__ float4 smem4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    float *sX = reinterpret_cast<float *>(smem4) + warp * S::WARP_FLOATS;
+    float *sD = sX + S::X_FLOATS;
+    const int K = a.K;
+    const int64_t n = a.n;
+    const unsigned FULL = 0xffffffffu;
+
+    for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
+        // columns: F(v), lane j <-> column j (+32 per extra column slot)
+        int cid[CPL];
+        float Lc[CPL][MP];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int j = lane + 32 * c;
+            int id = -1;
+            if (j < K) {
+                id = a.idx[v * K + j];
+                if (!valid_id(id, n)) {
+                    atomicOr(a.err, kErrIndex);
+                    id = -1;
+                }
+            }
+            cid[c] = id;
+            const float4 *lr = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(id < 0 ? 0 : id) * MP);
+#pragma unroll
+            for (int i4 = 0; i4 < MP / 4; ++i4) {
+                float4 t = (id >= 0) ? __ldg(lr + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                Lc[c][4 * i4 + 0] = t.x;
+                Lc[c][4 * i4 + 1] = t.y;
+                Lc[c][4 * i4 + 2] = t.z;
+                Lc[c][4 * i4 + 3] = t.w;
+            }
+        }
+        // the hub's own log row: column v of the co-friend pairs, staged in row slot 32
+        for (int i4 = lane; i4 < MP / 4; i4 += 32)
+            reinterpret_cast<float4 *>(sX + 32 * S::RS)[i4] =
+                __ldg(reinterpret_cast<const float4 *>(a.L32 + v * MP) + i4);
+
+        const int64_t c0 = a.cof_off[v];
+        const int64_t nrows = (int64_t)K + (a.cof_off[v + 1] - c0);
+        for (int64_t base = 0; base < nrows; base += 32) {
+            const int nr = (int)min((int64_t)32, nrows - base);
+            const int64_t r = base + lane;
+            int rid = -1;
+            if (r < nrows) {
+                rid = (r < K) ? a.idx[v * K + r] : a.cof[c0 + (r - K)];
+                if (!valid_id(rid, n)) {
+                    atomicOr(a.err, kErrIndex);
+                    rid = -1;
+                }
+            }
+            float ph = 0.f;
+            int64_t roff = 0;
+            float4 *srow = reinterpret_cast<float4 *>(sX + lane * S::RS);
+            if (rid >= 0) {
+                ph = a.phi[rid];
+                roff = (int64_t)K * K * rid + (int64_t)(K + 1) * a.cof_off[rid];
+                const float4 *xr = reinterpret_cast<const float4 *>(a.X32 + (int64_t)rid * MP);
+#pragma unroll
+                for (int i4 = 0; i4 < MP / 4; ++i4) srow[i4] = __ldg(xr + i4);
+            } else {
+#pragma unroll
+                for (int i4 = 0; i4 < MP / 4; ++i4) srow[i4] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
+
+            unsigned mymask[CPL];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) mymask[c] = 0u;
+            for (int rr = 0; rr < nr; ++rr) {
+                const int rrid = __shfl_sync(FULL, rid, rr);
+                const float rph = __shfl_sync(FULL, ph, rr);
+                const float4 *xr = reinterpret_cast<const float4 *>(sX + rr * S::RS);
+                float acc[CPL];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) acc[c] = 0.f;
+#pragma unroll
+                for (int i4 = 0; i4 < MP / 4; ++i4) {
+                    const float4 xv = xr[i4];
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                        acc[c] = __fmaf_rn(xv.x, Lc[c][4 * i4 + 0], acc[c]);
+                        acc[c] = __fmaf_rn(xv.y, Lc[c][4 * i4 + 1], acc[c]);
+                        acc[c] = __fmaf_rn(xv.z, Lc[c][4 * i4 + 2], acc[c]);
+                        acc[c] = __fmaf_rn(xv.w, Lc[c][4 * i4 + 3], acc[c]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const bool pass = rrid >= 0 && cid[c] >= 0 && cid[c] != rrid && acc[c] >= rph;
+                    const unsigned m = __ballot_sync(FULL, pass);
+                    if (lane == rr) mymask[c] = m;
+                    sD[(c * 32 + rr) * 33 + lane] = acc[c];
+                }
+            }
+            // co-friend pair (x in F(v), y = v): the row's own lane scores it
+            bool cfpass = false;
+            float cfd = 0.f;
+            if (r < K && rid >= 0) {
+                const float4 *xr = reinterpret_cast<const float4 *>(sX + lane * S::RS);
+                const float4 *lv = reinterpret_cast<const float4 *>(sX + 32 * S::RS);
+                float acc = 0.f;
+#pragma unroll
+                for (int i4 = 0; i4 < MP / 4; ++i4) {
+                    const float4 xv = xr[i4], lw = lv[i4];
+                    acc = __fmaf_rn(xv.x, lw.x, acc);
+                    acc = __fmaf_rn(xv.y, lw.y, acc);
+                    acc = __fmaf_rn(xv.z, lw.z, acc);
+                    acc = __fmaf_rn(xv.w, lw.w, acc);
+                }
+                cfd = acc;
+                cfpass = acc >= ph;
+            }
+            int count = cfpass ? 1 : 0;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) count += __popc(mymask[c]);
+            int64_t rowbase = 0;
+            if (count > 0) {
+                const int p = atomicAdd(&a.bcnt[rid], count);
+                rowbase = roff + p;
+                if (a.debug) {
+                    const int64_t cap = (int64_t)K * K + (int64_t)(K + 1) * (a.cof_off[rid + 1] - a.cof_off[rid]);
+                    if (p + count > cap) {
+                        atomicOr(a.err, kErrBucket);
+                        count = 0;
+                        cfpass = false;
+                        rowbase = -1;
+                    }
+                }
+            }
+            const unsigned lt = lanemask_lt();
+            for (int rr = 0; rr < nr; ++rr) {
+                int64_t rb = __shfl_sync(FULL, rowbase, rr);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const unsigned m = __shfl_sync(FULL, mymask[c], rr);
+                    if (rb >= 0 && ((m >> lane) & 1u))
+                        a.bent[rb + __popc(m & lt)] = make_int2(__float_as_int(sD[(c * 32 + rr) * 33 + lane]), cid[c]);
+                    rb += __popc(m);
+                }
+            }
+            if (cfpass && rowbase >= 0) a.bent[rowbase + count - 1] = make_int2(__float_as_int(cfd), (int)v);
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ FP64
+template <int MP, int CPL>
+struct F64Smem {
+    static constexpr int RS = MP + 2;  // row stride in doubles (16-byte aligned)
+    static constexpr int X_DOUBLES = 33 * RS;
+    static constexpr int D_DOUBLES = CPL * 32 * 33;
+    static constexpr int WARP_DOUBLES = X_DOUBLES + D_DOUBLES;
+};
+
+template <int MP, int CPL>
+__global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
+{
+    using S = F64Smem<MP, CPL>;
+    extern __shared__ double2 smemd[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    double *sX = reinterpret_cast<double *>(smemd) + warp * S::WARP_DOUBLES;
+    double *sD = sX + S::X_DOUBLES;
+    const int K = a.K;
+    const int64_t n = a.n;
+    const unsigned FULL = 0xffffffffu;
+
+    for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
+        int cid[CPL];
+        double Lc[CPL][MP];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int j = lane + 32 * c;
+            int id = -1;
+            if (j < K) {
+                id = a.idx[v * K + j];
+                if (!valid_id(id, n)) {
+                    atomicOr(a.err, kErrIndex);
+                    id = -1;
+                }
+            }
+            cid[c] = id;
+            const double2 *lr = reinterpret_cast<const double2 *>(a.L64 + (int64_t)(id < 0 ? 0 : id) * MP);
+#pragma unroll
+            for (int i2 = 0; i2 < MP / 2; ++i2) {
+                double2 t = (id >= 0) ? __ldg(lr + i2) : make_double2(0.0, 0.0);
+                Lc[c][2 * i2 + 0] = t.x;
+                Lc[c][2 * i2 + 1] = t.y;
+            }
+        }
+        for (int i2 = lane; i2 < MP / 2; i2 += 32)
+            reinterpret_cast<double2 *>(sX + 32 * S::RS)[i2] =
+                __ldg(reinterpret_cast<const double2 *>(a.L64 + v * MP) + i2);
+
+        const int64_t c0 = a.cof_off[v];
+        const int64_t nrows = (int64_t)K + (a.cof_off[v + 1] - c0);
+        for (int64_t base = 0; base < nrows; base += 32) {
+            const int nr = (int)min((int64_t)32, nrows - base);
+            const int64_t r = base + lane;
+            int rid = -1;
+            if (r < nrows) {
+                rid = (r < K) ? a.idx[v * K + r] : a.cof[c0 + (r - K)];
+                if (!valid_id(rid, n)) {
+                    atomicOr(a.err, kErrIndex);
+                    rid = -1;
+                }
+            }
+            double nh = 0.0, tk = 0.0;
+            int ik = 0;
+            int64_t roff = 0;
+            double2 *srow = reinterpret_cast<double2 *>(sX + lane * S::RS);
+            if (rid >= 0) {
+                nh = a.negH[rid];
+                tk = a.tau[rid];
+                ik = a.idxK[rid];
+                roff = (int64_t)K * K * rid + (int64_t)(K + 1) * a.cof_off[rid];
+                const double2 *xr = reinterpret_cast<const double2 *>(a.X64 + (int64_t)rid * MP);
+#pragma unroll
+                for (int i2 = 0; i2 < MP / 2; ++i2) srow[i2] = __ldg(xr + i2);
+            } else {
+#pragma unroll
+                for (int i2 = 0; i2 < MP / 2; ++i2) srow[i2] = make_double2(0.0, 0.0);
+            }
+            __syncwarp();
+
+            unsigned mymask[CPL];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) mymask[c] = 0u;
+            for (int rr = 0; rr < nr; ++rr) {
+                const int rrid = __shfl_sync(FULL, rid, rr);
+                const double rnh = __shfl_sync(FULL, nh, rr);
+                const double rtk = __shfl_sync(FULL, tk, rr);
+                const int rik = __shfl_sync(FULL, ik, rr);
+                const double2 *xr = reinterpret_cast<const double2 *>(sX + rr * S::RS);
+                double acc[CPL];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) acc[c] = 0.0;
+#pragma unroll
+                for (int i2 = 0; i2 < MP / 2; ++i2) {
+                    const double2 xv = xr[i2];
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                        acc[c] = __fma_rn(xv.x, Lc[c][2 * i2 + 0], acc[c]);
+                        acc[c] = __fma_rn(xv.y, Lc[c][2 * i2 + 1], acc[c]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const double k = rnh - acc[c];
+                    const bool pass = rrid >= 0 && cid[c] >= 0 && cid[c] != rrid && lex_less(k, cid[c], rtk, rik);
+                    const unsigned m = __ballot_sync(FULL, pass);
+                    if (lane == rr) mymask[c] = m;
+                    sD[(c * 32 + rr) * 33 + lane] = k;
+                }
+            }
+            bool cfpass = false;
+            double cfk = 0.0;
+            if (r < K && rid >= 0) {
+                const double2 *xr = reinterpret_cast<const double2 *>(sX + lane * S::RS);
+                const double2 *lv = reinterpret_cast<const double2 *>(sX + 32 * S::RS);
+                double acc = 0.0;
+#pragma unroll
+                for (int i2 = 0; i2 < MP / 2; ++i2) {
+                    const double2 xv = xr[i2], lw = lv[i2];
+                    acc = __fma_rn(xv.x, lw.x, acc);
+                    acc = __fma_rn(xv.y, lw.y, acc);
+                }
+                cfk = nh - acc;
+                cfpass = lex_less(cfk, (int)v, tk, ik);
+            }
+            int count = cfpass ? 1 : 0;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) count += __popc(mymask[c]);
+            int64_t rowbase = 0;
+            if (count > 0) {
+                const int p = atomicAdd(&a.bcnt[rid], count);
+                rowbase = roff + p;
+                if (a.debug) {
+                    const int64_t cap = (int64_t)K * K + (int64_t)(K + 1) * (a.cof_off[rid + 1] - a.cof_off[rid]);
+                    if (p + count > cap) {
+                        atomicOr(a.err, kErrBucket);
+                        count = 0;
+                        cfpass = false;
+                        rowbase = -1;
+                    }
+                }
+            }
+            const unsigned lt = lanemask_lt();
+            for (int rr = 0; rr < nr; ++rr) {
+                int64_t rb = __shfl_sync(FULL, rowbase, rr);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const unsigned m = __shfl_sync(FULL, mymask[c], rr);
+                    if (rb >= 0 && ((m >> lane) & 1u)) {
+                        const int64_t pos = rb + __popc(m & lt);
+                        a.bkey[pos] = sD[(c * 32 + rr) * 33 + lane];
+                        a.bidx[pos] = cid[c];
+                    }
+                    rb += __popc(m);
+                }
+            }
+            if (cfpass && rowbase >= 0) {
+                a.bkey[rowbase + count - 1] = cfk;
+                a.bidx[rowbase + count - 1] = (int)v;
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ dispatch
+template <int MP, int CPL>
+static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
+{
+    if (h->prec == KNND_PREC_FP64) {
+        using S = F64Smem<MP, CPL>;
+        const int threads = 128;
+        const size_t smem = sizeof(double) * S::WARP_DOUBLES * (threads / 32);
+        cudaFuncSetAttribute(join_fp64_kernel<MP, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_fp64_kernel<MP, CPL>, threads, smem);
+        if (per_sm < 1) per_sm = 1;
+        const int64_t need = (h->n + threads / 32 - 1) / (threads / 32);
+        const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * per_sm);
+        join_fp64_kernel<MP, CPL><<<(unsigned)grid, threads, smem, h->stream>>>(a);
+    } else {
+        using S = MixedSmem<MP, CPL>;
+        const int threads = 256;
+        const size_t smem = sizeof(float) * S::WARP_FLOATS * (threads / 32);
+        cudaFuncSetAttribute(join_mixed_kernel<MP, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_mixed_kernel<MP, CPL>, threads, smem);
+        if (per_sm < 1) per_sm = 1;
+        const int64_t need = (h->n + threads / 32 - 1) / (threads / 32);
+        const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * per_sm);
+        join_mixed_kernel<MP, CPL><<<(unsigned)grid, threads, smem, h->stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int MP>
+static cudaError_t run_join_cpl(knnd_handle *h, const JoinArgs &a)
+{
+    if (h->K <= 32) return run_join<MP, 1>(h, a);
+    return run_join<MP, 2>(h, a);
+}
+
+cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
+{
+    JoinArgs a;
+    a.n = h->n;
+    a.K = h->K;
+    a.idx = idx;
+    a.cof_off = h->cof_off;
+    a.cof = h->cof;
+    a.X32 = h->X32;
+    a.L32 = h->L32;
+    a.X64 = h->X64;
+    a.L64 = h->L64;
+    a.negH = h->negH;
+    a.tau = h->tau;
+    a.idxK = h->idxK;
+    a.phi = h->phi;
+    a.bcnt = h->bcnt;
+    a.bent = h->bent;
+    a.bkey = h->bkey;
+    a.bidx = h->bidx;
+    a.err = h->err;
+    a.debug = h->prm.debug;
+    cudaMemsetAsync(h->bcnt, 0, sizeof(int32_t) * h->n, h->stream);
+    h->launches += 1;
+    switch (h->MP) {
+    case 8: return run_join_cpl<8>(h, a);
+    case 16: return run_join_cpl<16>(h, a);
+    case 24: return run_join_cpl<24>(h, a);
+    case 32: return run_join_cpl<32>(h, a);
+    case 48: return run_join_cpl<48>(h, a);
+    case 64: return run_join_cpl<64>(h, a);
+    case 72: return run_join_cpl<72>(h, a);
+    case 96: return run_join_cpl<96>(h, a);
+    case 128: return run_join_cpl<128>(h, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace knnd

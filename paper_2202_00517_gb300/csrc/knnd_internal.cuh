@@ -1,0 +1,189 @@
+// knnd_internal.cuh -- shared definitions of the CUDA translation units.
+//
+// Device data layout (one handle, n points, m coordinates padded to MP, a
+// multiple of 8; padding coordinates are 0 in every table, so the padded
+// terms of an fma chain are exact no-ops):
+//   X64  n x MP  float64   the points
+//   L64  n x MP  float64   log of the points
+//   X32  n x MP  float32   the points rounded to FP32 (mixed form)
+//   L32  n x MP  float32   log rounded to FP32 (mixed form)
+//   negH n       float64   sum_i x_i log x_i (canonical fma chain)
+//   nx   n       float64   sum_i |x_i|
+//   cof_off n+1  int64     co-friend CSR offsets, cof n*K int32 entries
+//   bucket       per point x, capacity K*K + (K+1)*indeg(x) at offset
+//                K*K*x + (K+1)*cof_off[x]: the candidates the join emits for x.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/knnd.h"
+
+namespace knnd {
+
+constexpr int kWarp = 32;
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) and word streams with
+// counter (c0, c1, c2, block); Lemire's bounded integers (ACM TOMACS 2019).
+// --------------------------------------------------------------------------
+struct Philox {
+    uint32_t k0, k1, c0, c1, c2, block;
+    uint32_t w[4];
+    int pos;
+    __device__ __forceinline__ Philox(uint64_t seed, uint32_t a, uint32_t b, uint32_t c)
+        : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), c0(a), c1(b), c2(c), block(0), pos(4) {}
+
+    __device__ __forceinline__ void refill() {
+        uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = block;
+        uint32_t key0 = k0, key1 = k1;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+            uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+            uint32_t n0 = hi1 ^ x1 ^ key0, n2 = hi0 ^ x3 ^ key1;
+            x0 = n0;
+            x1 = lo1;
+            x2 = n2;
+            x3 = lo0;
+            key0 += 0x9E3779B9u;
+            key1 += 0xBB67AE85u;
+        }
+        w[0] = x0;
+        w[1] = x1;
+        w[2] = x2;
+        w[3] = x3;
+        block += 1;
+        pos = 0;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        if (pos == 4) refill();
+        return w[pos++];
+    }
+    // uniform in [0, N), N >= 1
+    __device__ __forceinline__ uint32_t bounded(uint32_t N) {
+        uint32_t x = next();
+        uint64_t prod = (uint64_t)x * N;
+        uint32_t low = (uint32_t)prod;
+        if (low < N) {
+            uint32_t t = (0u - N) % N;
+            while (low < t) {
+                x = next();
+                prod = (uint64_t)x * N;
+                low = (uint32_t)prod;
+            }
+        }
+        return (uint32_t)(prod >> 32);
+    }
+};
+
+// Philox stream tags (counter word c2).
+constexpr uint32_t kTagInit = 0;
+constexpr uint32_t kTagFcc = 1;
+
+// --------------------------------------------------------------------------
+// Candidate order: (key ascending, index ascending).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ bool lex_less(double ka, int ia, double kb, int ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Status bits set by kernels in the device error word.
+constexpr int kErrDomain = 1;
+constexpr int kErrBucket = 2;
+constexpr int kErrIndex = 4;
+
+// Device counters of one call (int64 each).
+enum Counter : int {
+    kCntUpdates = 0,
+    kCntHits = 1,
+    kCntRescored = 2,
+    kCntBoundViol = 3,
+    kCntNum = 8
+};
+
+}  // namespace knnd
+
+struct knnd_handle {
+    int64_t n;
+    int32_t m, MP, K;
+    knnd_dtype dtype;
+    knnd_precision prec;
+    knnd_params prm;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    bool prepared;
+
+    // precompute
+    double *X64, *L64, *negH, *nx;
+    float *X32, *L32;
+    unsigned long long *smax_bits;  // max |log y_i| as the bits of a non-negative double
+    int32_t *err;                   // device error word
+    // reverse CSR
+    int32_t *deg;     // n: in-degree, then fill cursor
+    int64_t *cof_off; // n+1
+    int32_t *cof;     // n*K
+    int64_t *scan_tmp;
+    int64_t scan_tmp_len;
+    // per-row thresholds of the join filter
+    double *tau;  // n: K-th key of the row
+    int32_t *idxK;  // n: K-th index of the row
+    float *phi;   // n: mixed form, dot-space rejection threshold
+    double *Ex;   // n: mixed form, error bound of the FP32 dot
+    // buckets
+    int32_t *bcnt;  // n
+    int64_t bucket_cap;
+    double *bkey;   // FP64 form: bucket keys
+    int32_t *bidx;  // FP64 form: bucket indices
+    int2 *bent;     // mixed form: (FP32 dot bits, index)
+    // counters
+    int64_t *cnt;       // kCntNum device counters
+    int64_t *cnt_host;  // pinned mirror
+    // graph buffers for the host-memory build
+    void *pts_dev;
+    int64_t pts_dev_bytes;
+    int32_t *idx_dev;
+    double *key_dev;
+    // per-phase CUDA-event timing (params.timing)
+    static constexpr int kMaxPending = 256;
+    cudaEvent_t ev[2 * kMaxPending];
+    int pend_phase[kMaxPending];
+    int npend;
+    bool events_made;
+    double phase_ms[KNND_NUM_PHASES];
+    int64_t phase_count[KNND_NUM_PHASES];
+    // statistics
+    int64_t launches;
+    int64_t rounds_run;
+    int64_t ws_bytes;
+    double bound_c;  // c_m of the FP32 error bound
+};
+
+namespace knnd {
+
+// ---- launch wrappers (each returns cudaGetLastError() of its launches) ----
+cudaError_t launch_precompute(knnd_handle *h, const void *points, int64_t ld);
+cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, double *key, uint8_t *newflag);
+cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key);
+cudaError_t launch_join(knnd_handle *h, const int32_t *idx);
+cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag);
+cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out);
+
+inline int pad_coords(int m) {
+    int mp = (m + 7) / 8 * 8;
+    if (mp > 64 && mp <= 72) return 72;
+    if (mp > 72 && mp <= 96) return 96;
+    if (mp > 96) return 128;
+    if (mp > 32 && mp <= 48) return 48;
+    if (mp > 48 && mp <= 64) return 64;
+    return mp;  // 8, 16, 24, 32
+}
+
+}  // namespace knnd

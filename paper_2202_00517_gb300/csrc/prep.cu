@@ -1,0 +1,205 @@
+// prep.cu -- per-build precompute (log table, -H(x), FP32 copies, error-bound
+// scale), the initial random K-out graph (Sec. 3.2) and the friend clustering
+// sample (Sec. 3.3).
+#include <cfloat>
+
+#include "knnd_internal.cuh"
+
+namespace knnd {
+
+// ---------------------------------------------------------------------------
+// Precompute (Sec. 2.2 rewritten as key(x, y) = negH(x) - <x, log y>):
+// one thread per point.  L = log(x) in FP64 (CUDA's double-precision log),
+// negH = sum_i x_i L_i as a sequential fma chain from 0, nx = sum_i |x_i|,
+// and the largest |L| over all coordinates (the FP32 error-bound scale).
+// Coordinates that are not finite or not > 0 set kErrDomain.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, int64_t n, int m, int MP,
+                                  double *__restrict__ X64, double *__restrict__ L64, float *__restrict__ X32,
+                                  float *__restrict__ L32, double *__restrict__ negH, double *__restrict__ nx,
+                                  unsigned long long *smax_bits, int32_t *err)
+{
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double lmax = 0.0;
+    if (x < n) {
+        double acc = 0.0, s = 0.0;
+        bool bad = false;
+        const T *row = pts + x * ld;
+        for (int i = 0; i < MP; ++i) {
+            double v = 0.0, l = 0.0;
+            if (i < m) {
+                v = (double)row[i];
+                if (!(v > 0.0) || !(v <= DBL_MAX)) {
+                    bad = true;
+                    v = 1.0;  // keep the tables finite; the call reports EDOMAIN
+                }
+                l = log(v);
+                acc = __fma_rn(v, l, acc);
+                s += fabs(v);
+                lmax = fmax(lmax, fabs(l));
+            }
+            X64[x * MP + i] = v;
+            L64[x * MP + i] = l;
+            X32[x * MP + i] = __double2float_rn(v);
+            L32[x * MP + i] = __double2float_rn(l);
+        }
+        negH[x] = acc;
+        nx[x] = s;
+        if (bad) atomicOr(err, kErrDomain);
+    }
+    // block max of |L| -> one atomicMax on the (monotone) bits of a non-negative double
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    __shared__ double wmax[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wmax[w] = lmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b = fmax(b, wmax[i]);
+        atomicMax(smax_bits, (unsigned long long)__double_as_longlong(b));
+    }
+}
+
+cudaError_t launch_precompute(knnd_handle *h, const void *points, int64_t ld)
+{
+    const int threads = 256;
+    const int64_t blocks = (h->n + threads - 1) / threads;
+    cudaMemsetAsync(h->smax_bits, 0, sizeof(unsigned long long), h->stream);
+    if (h->dtype == KNND_F32)
+        precompute_kernel<float><<<(unsigned)blocks, threads, 0, h->stream>>>(
+            (const float *)points, ld, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32, h->negH, h->nx,
+            h->smax_bits, h->err);
+    else
+        precompute_kernel<double><<<(unsigned)blocks, threads, 0, h->stream>>>(
+            (const double *)points, ld, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32, h->negH, h->nx,
+            h->smax_bits, h->err);
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Canonical FP64 key of (x, y): negH[x] - (fma chain over i of x_i * log y_i).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double key_fp64(const double *__restrict__ X64, const double *__restrict__ L64,
+                                           const double *__restrict__ negH, int MP, int64_t x, int64_t y)
+{
+    const double2 *xr = reinterpret_cast<const double2 *>(X64 + x * MP);
+    const double2 *lr = reinterpret_cast<const double2 *>(L64 + y * MP);
+    double acc = 0.0;
+    for (int i = 0; i < MP / 2; ++i) {
+        double2 a = xr[i], b = lr[i];
+        acc = __fma_rn(a.x, b.x, acc);
+        acc = __fma_rn(a.y, b.y, acc);
+    }
+    return negH[x] - acc;
+}
+
+// ---------------------------------------------------------------------------
+// Initial random K-out graph (Sec. 3.2): one thread per point x.  Friends are
+// drawn from Philox stream (seed, x, 0, kTagInit): y' uniform in [0, n-1),
+// y = y' + (y' >= x), a repeat drawn again.  Rows sorted by (key, idx).
+// ---------------------------------------------------------------------------
+__global__ void init_graph_kernel(int64_t n, int K, int MP, const double *__restrict__ X64,
+                                  const double *__restrict__ L64, const double *__restrict__ negH, uint64_t seed,
+                                  int32_t *__restrict__ idx, double *__restrict__ key, uint8_t *__restrict__ flag)
+{
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    int ids[KNND_MAX_K];
+    double ks[KNND_MAX_K];
+    Philox ph(seed, (uint32_t)x, 0u, kTagInit);
+    int cnt = 0;
+    while (cnt < K) {
+        uint32_t yp = ph.bounded((uint32_t)(n - 1));
+        int y = (int)yp + ((int64_t)yp >= x ? 1 : 0);
+        bool dup = false;
+        for (int t = 0; t < cnt; ++t) dup |= (ids[t] == y);
+        if (dup) continue;
+        ids[cnt++] = y;
+    }
+    for (int t = 0; t < K; ++t) ks[t] = key_fp64(X64, L64, negH, MP, x, ids[t]);
+    for (int t = 1; t < K; ++t) {  // insertion sort by (key, idx)
+        double kk = ks[t];
+        int ii = ids[t];
+        int s = t - 1;
+        while (s >= 0 && lex_less(kk, ii, ks[s], ids[s])) {
+            ks[s + 1] = ks[s];
+            ids[s + 1] = ids[s];
+            --s;
+        }
+        ks[s + 1] = kk;
+        ids[s + 1] = ii;
+    }
+    for (int t = 0; t < K; ++t) {
+        idx[x * K + t] = ids[t];
+        key[x * K + t] = ks[t];
+        if (flag) flag[x * K + t] = 1;
+    }
+}
+
+cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, double *key, uint8_t *newflag)
+{
+    const int threads = 128;
+    const int64_t blocks = (h->n + threads - 1) / threads;
+    init_graph_kernel<<<(unsigned)blocks, threads, 0, h->stream>>>(h->n, h->K, h->MP, h->X64, h->L64, h->negH,
+                                                                   seed, idx, key, newflag);
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Friend clustering sample (Sec. 3.3): thread per sample s, stream
+// (seed, s, round, kTagFcc): x uniform in [0, n), i uniform in [0, K),
+// j' uniform in [0, K-1), j = j' + (j' >= i).  Hit when z = F(x)[j] is a friend
+// of y = F(x)[i] or y is a friend of z.  Indices outside [0, n) set kErrIndex
+// and count as misses.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool row_has(const int32_t *__restrict__ idx, int K, int64_t a, int32_t b)
+{
+    bool f = false;
+    for (int t = 0; t < K; ++t) f |= (idx[a * K + t] == b);
+    return f;
+}
+
+__global__ void fcc_kernel(const int32_t *__restrict__ idx, int64_t n, int K, uint64_t seed, int32_t round,
+                           int32_t S, int64_t *hits, int32_t *err)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int hit = 0;
+    if (s < S) {
+        Philox ph(seed, (uint32_t)s, (uint32_t)round, kTagFcc);
+        int64_t x = ph.bounded((uint32_t)n);
+        int i = (int)ph.bounded((uint32_t)K);
+        int jp = (int)ph.bounded((uint32_t)(K - 1));
+        int j = jp + (jp >= i ? 1 : 0);
+        int32_t y = idx[x * K + i], z = idx[x * K + j];
+        if (y < 0 || y >= n || z < 0 || z >= n) {
+            atomicOr(err, kErrIndex);
+        } else {
+            hit = (row_has(idx, K, y, z) || row_has(idx, K, z, y)) ? 1 : 0;
+        }
+    }
+    unsigned b = __ballot_sync(0xffffffffu, hit);
+    __shared__ int wsum[32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+        if (t) atomicAdd((unsigned long long *)hits, (unsigned long long)t);
+    }
+}
+
+cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out)
+{
+    const int threads = 256;
+    const int S = h->prm.fcc_samples;
+    cudaMemsetAsync(hits_out, 0, sizeof(int64_t), h->stream);
+    fcc_kernel<<<(S + threads - 1) / threads, threads, 0, h->stream>>>(idx, h->n, h->K, seed, round, S, hits_out,
+                                                                       h->err);
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace knnd

@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every function include/knnd.h declares, and rejects
+bad arguments on the host before touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2202_00517_gb300 import _lib, build_ext
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "knnd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_ext.build()
+    return _lib.load()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(knnd_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported(lib):
+    names = _declared()
+    assert "knnd_build" in names and "knnd_round" in names and "knnd_init_graph" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(_lib.EXPORTS) == names
+
+
+def test_version_and_status_strings(lib):
+    assert lib.knnd_version() >= 100
+    for code in range(0, -8, -1):
+        s = _lib.status_string(code)
+        assert s and s != "unknown status"
+    assert _lib.status_string(-99) == "unknown status"
+
+
+def test_struct_layouts():
+    # host structs of the header: five int32 params; build info 8 + 64*8 + 65*8 + 4*8 bytes;
+    # stats 3 int64 + 6 int64 + 6 double
+    assert ctypes.sizeof(_lib.knnd_params) == 20
+    assert ctypes.sizeof(_lib.knnd_build_info) == 8 + 64 * 8 + 65 * 8 + 4 * 8
+    assert ctypes.sizeof(_lib.knnd_stats) == 3 * 8 + 6 * 8 + 6 * 8
+
+
+@pytest.mark.parametrize("n,m,K,dtype,prec", [
+    (1000, 6, 1, 0, 1),          # K < 2
+    (1000, 6, 65, 0, 1),         # K > KNND_MAX_K
+    (10, 6, 10, 0, 1),           # K >= n
+    (1000, 0, 10, 0, 1),         # m < 1
+    (1000, 129, 10, 0, 1),       # m > KNND_MAX_M
+    (2**31, 6, 10, 0, 1),        # n >= 2^31
+    (2, 6, 1, 0, 1),             # n < 3
+    (1000, 6, 10, 7, 1),         # bad dtype
+    (1000, 6, 10, 0, 9),         # bad precision
+])
+def test_create_rejects_bad_shapes(lib, n, m, K, dtype, prec):
+    h = ctypes.c_void_p(1234)
+    st = lib.knnd_create(ctypes.byref(h), n, m, K, dtype, prec, None, None)
+    assert st == _lib.KNND_EINVAL
+    assert h.value is None
+
+
+def test_create_rejects_bad_params(lib):
+    h = ctypes.c_void_p()
+    for prm in (_lib.knnd_params(0, 10, 1, 0, 0), _lib.knnd_params(100, 0, 1, 0, 0),
+                _lib.knnd_params(100, 65, 1, 0, 0)):
+        assert lib.knnd_create(ctypes.byref(h), 1000, 6, 10, 0, 1, ctypes.byref(prm), None) == _lib.KNND_EINVAL
+    assert lib.knnd_create(None, 1000, 6, 10, 0, 1, None, None) == _lib.KNND_EINVAL
+
+
+def test_null_handle_calls(lib):
+    info = _lib.knnd_build_info()
+    st = _lib.knnd_stats()
+    assert lib.knnd_build(None, None, 6, 0, None, None, None, ctypes.byref(info)) == _lib.KNND_EINVAL
+    assert lib.knnd_build_host(None, None, 6, 0, None, None, ctypes.byref(info)) == _lib.KNND_EINVAL
+    assert lib.knnd_round(None, None, 6, 0, 1, None, None, None, None, None) == _lib.KNND_EINVAL
+    assert lib.knnd_init_graph(None, None, 6, 0, None, None, None) == _lib.KNND_EINVAL
+    assert lib.knnd_prepare(None, None, 6) == _lib.KNND_EINVAL
+    assert lib.knnd_fcc(None, None, 0, 0, None) == _lib.KNND_EINVAL
+    assert lib.knnd_sync(None) == _lib.KNND_EINVAL
+    assert lib.knnd_set_stream(None, None) == _lib.KNND_EINVAL
+    assert lib.knnd_get_stats(None, ctypes.byref(st)) == _lib.KNND_EINVAL
+    assert lib.knnd_reset_stats(None) == _lib.KNND_EINVAL
+    lib.knnd_destroy(None)
+
+
+def test_product_path_has_no_oracle_dependency():
+    pkg = os.path.join(ROOT, "paper_2202_00517_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "liboracle" not in text, f

@@ -1,0 +1,89 @@
+"""Parity at the full benchmark size: n = 1,000,000 Dirichlet(1) points on the
+20-simplex (21 FP32 coordinates), K = 20, seed 1, in the launch configuration
+the benchmark times.
+
+The oracle cannot run the whole build at this size within a test, so:
+* the initial graph is compared in full;
+* round 1 is run on the CUDA path from the oracle's initial graph and compared
+  on sampled row ranges the oracle computes one by one;
+* the free-running builds are checked by properties that hold at any size:
+  row invariants, the mixed form equal to the FP64 form bit for bit, the stop
+  rule, rounds within twice the diameter of the undirected initial graph
+  (Sec. 3.2, Sec. 4.3), and recall against brute force on sampled queries.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_00517_gb300.datagen import dirichlet_points
+from parity_util import check_invariants, compare_graphs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+N, M, K, SEED = 1_000_000, 21, 20, 1
+
+
+@pytest.fixture(scope="module")
+def data():
+    assert torch.cuda.is_available()
+    import paper_2202_00517_gb300 as knnd
+    pts = dirichlet_points(N, M, SEED, np.float32)
+    pts64 = pts.astype(np.float64)
+    g0i, g0k = oracle.init_graph(pts64, K, SEED)
+    return knnd, pts, pts64, g0i, g0k
+
+
+def test_init_and_round1_sampled(data):
+    knnd, pts, pts64, g0i, g0k = data
+    p = torch.from_numpy(pts).cuda()
+    ranges = [(0, 6000), (N // 2, N // 2 + 3000), (N - 4000, N)]
+    for prec in ("fp64", "mixed"):
+        h = knnd.Handle(N, M, K, dtype="f32", precision=prec)
+        gi, gk, _ = h.init_graph(p, SEED)
+        assert np.array_equal(gi.cpu().numpy(), g0i)
+        compare_graphs(pts64, gi.cpu().numpy(), gk.cpu().numpy(), g0i, g0k, rows=np.arange(0, N, 997),
+                       max_tie_rows=0)
+        idx = torch.from_numpy(g0i).cuda()
+        key = torch.from_numpy(g0k).cuda()
+        h.round(None, SEED, 1, idx, key)
+        h.sync()
+        gidx, gkey = idx.cpu().numpy(), key.cpu().numpy()
+        ties = 0
+        for x0, x1 in ranges:
+            ri, rk, _, _, _ = oracle.round_(pts64, g0i, x0, x1)
+            ties += compare_graphs(pts64, gidx, gkey, ri, rk, rows=np.arange(x0, x1))
+        assert ties <= 3
+        check_invariants(gidx, gkey)
+        h.close()
+
+
+def test_full_builds(data):
+    knnd, pts, pts64, g0i, _ = data
+    p = torch.from_numpy(pts).cuda()
+    res = {}
+    for prec in ("fp64", "mixed"):
+        h = knnd.Handle(N, M, K, dtype="f32", precision=prec)
+        res[prec] = h.build(p, SEED)
+        h.close()
+    a, b = res["fp64"], res["mixed"]
+    assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"]
+    assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["key"], b["key"])
+    idx, key = b["idx"].cpu().numpy(), b["key"].cpu().numpy()
+    check_invariants(idx, key)
+    h = b["fcc_hits"]
+    r = b["rounds"]
+    assert b["stop_reason"] in (1, 2)
+    if b["stop_reason"] == 1:
+        assert h[r] <= h[r - 1] and all(h[t] > h[t - 1] for t in range(1, r))
+    # rounds vs twice the diameter of the undirected initial graph (lower bound of the diameter)
+    lo, hi = oracle.diameter_bounds(g0i, sweeps=2, seed=SEED)
+    assert lo > 0
+    assert r <= 2 * lo, (r, lo, hi)
+    # recall against brute force on sampled queries (reported; loose floor)
+    q = np.linspace(0, N - 1, 100).astype(np.int32)
+    bi, _ = oracle.bruteforce(pts64, K, q)
+    recall = float(np.mean([len(set(bi[t]) & set(idx[x])) / K for t, x in enumerate(q)]))
+    print(f"rounds={r} updates={b['updates']} fcc={h} recall@{K}={recall:.3f} rescored={b['rescored']}")
+    assert recall > 0.3
