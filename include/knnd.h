@@ -187,6 +187,30 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
 knnd_status knnd_build_host(knnd_handle *h, const void *points_host, int64_t ld, uint64_t seed,
                             int32_t *idx_host, double *key_host, knnd_build_info *info);
 
+/* Largest sample count knnd_fcc_noalloc accepts. */
+#define KNND_NOALLOC_MAX_SAMPLES (1 << 20)
+
+/* The clustering sample of knnd_fcc without a handle and without allocating
+ * any device memory.  The paper has no counterpart: this entry point serves
+ * callers that cannot call cudaMalloc -- an application whose memory pool or
+ * caching allocator already holds nearly all device memory, a serving loop
+ * that forbids allocation after start-up, a plug-in whose host requires all
+ * allocations to go through the host's allocator -- and so cannot create a
+ * handle, but run their own descent loop and need the stop test.
+ * Same draws, hit rule and result as knnd_fcc: idx (device, n x K int32),
+ * samples S in [1, KNND_NOALLOC_MAX_SAMPLES] (EOVERFLOW above it), hits
+ * (device int64, overwritten; -1 when a sampled friend index lies outside
+ * [0, n)).  Enqueued on `stream` (cudaStream_t as void*).
+ * Scratch: a fixed array of about 32 KB in the library's device memory,
+ * loaded with the library and held by every GPU that loads it until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls on a device share the array:
+ * calls that overlap on the GPU race.  Allocates nothing, frees nothing.
+ * Errors: EINVAL (null pointer, shape as in knnd_create), EOVERFLOW, ECUDA. */
+knnd_status knnd_fcc_noalloc(const int32_t *idx, int64_t n, int32_t K, uint64_t seed, int32_t round,
+                             int32_t samples, int64_t *hits, void *stream);
+
 /* Synchronise the handle's stream and return (and clear) the sticky device
  * status: EDOMAIN (bad coordinate), EINVAL (a graph index outside [0, n)
  * met by a kernel, which skipped it), EOVERFLOW (debug bucket check), or OK.

@@ -35,8 +35,10 @@ KNND_STOP_MAX_ROUNDS = 3
 EXPORTS = [
     "knnd_create", "knnd_destroy", "knnd_set_stream", "knnd_prepare", "knnd_init_graph", "knnd_round",
     "knnd_fcc", "knnd_sync", "knnd_build", "knnd_build_host", "knnd_get_stats", "knnd_reset_stats",
-    "knnd_status_string", "knnd_version",
+    "knnd_status_string", "knnd_version", "knnd_fcc_noalloc",
 ]
+
+KNND_NOALLOC_MAX_SAMPLES = 1 << 20
 
 
 class knnd_params(ctypes.Structure):
@@ -97,6 +99,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "knnd_reset_stats": (i32, [P]),
         "knnd_status_string": (ctypes.c_char_p, [i32]),
         "knnd_version": (i32, []),
+        "knnd_fcc_noalloc": (i32, [P, i64, i32, u64, i32, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
