@@ -145,6 +145,20 @@ __device__ __forceinline__ void load_row(const MergeArgs &a, int64_t x, int lane
     }
 }
 
+// Lane-parallel test of y against the row's original list (indices `oi`, entry
+// q = lane + 32 e): every lane checks its own candidate, K shuffles in all.
+template <int NE>
+__device__ __forceinline__ bool in_old_list(const int (&oi)[NE], int K, int y)
+{
+    bool f = false;
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+        const int lim = min(32, K - 32 * e);
+        for (int t = 0; t < lim; ++t) f |= (__shfl_sync(0xffffffffu, oi[e], t) == y);
+    }
+    return f;
+}
+
 // Entries the join wrote for x, never more than the row's capacity.
 __device__ __forceinline__ int bucket_count(const MergeArgs &a, int64_t x)
 {
@@ -174,6 +188,9 @@ __global__ void __launch_bounds__(256) merge_fp64_kernel(MergeArgs a)
     for (int64_t x = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); x < a.n; x += (int64_t)gridDim.x * wpb) {
         WarpList<NE> X;
         load_row(a, x, lane, X);
+        int oi[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) oi[e] = X.i[e];
         double tk;
         int ti;
         X.kth(K, tk, ti);
@@ -187,7 +204,8 @@ __global__ void __launch_bounds__(256) merge_fp64_kernel(MergeArgs a)
                 ck = a.bkey[base + c0 + lane];
                 ci = a.bidx[base + c0 + lane];
             }
-            unsigned mask = __ballot_sync(0xffffffffu, has && lex_less(ck, ci, tk, ti));
+            const bool old = in_old_list(oi, K, ci);
+            unsigned mask = __ballot_sync(0xffffffffu, has && !old && lex_less(ck, ci, tk, ti));
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
@@ -217,6 +235,9 @@ __global__ void __launch_bounds__(256) merge_mixed_kernel(MergeArgs a)
     for (int64_t x = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); x < a.n; x += (int64_t)gridDim.x * wpb) {
         WarpList<NE> X;
         load_row(a, x, lane, X);
+        int oi[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) oi[e] = X.i[e];
         const int64_t base = (int64_t)K * K * x + (int64_t)(K + 1) * a.cof_off[x];
         const int cnt = bucket_count(a, x);
         if (cnt > 0) {
@@ -236,7 +257,9 @@ __global__ void __launch_bounds__(256) merge_mixed_kernel(MergeArgs a)
                     ub = (nh - (double)__int_as_float(en.x)) + E;
                     ci = en.y;
                 }
-                unsigned mask = __ballot_sync(0xffffffffu, has && lex_less(ub, ci, tk, ti));
+                // old friends re-proposed by the join are dropped without serial work
+                const bool old = in_old_list(oi, K, ci);
+                unsigned mask = __ballot_sync(0xffffffffu, has && !old && lex_less(ub, ci, tk, ti));
                 while (mask) {
                     const int src = __ffs(mask) - 1;
                     mask &= mask - 1;
@@ -260,7 +283,8 @@ __global__ void __launch_bounds__(256) merge_mixed_kernel(MergeArgs a)
                     lb = (nh - (double)__int_as_float(en.x)) - E;
                     ci = en.y;
                 }
-                bool want = has && lb <= T && lb <= xk && ci >= 0 && ci < a.n;
+                const bool old = in_old_list(oi, K, ci);  // warp-collective: every lane calls it
+                bool want = has && !old && lb <= T && lb <= xk && ci >= 0 && ci < a.n;
                 unsigned mask = __ballot_sync(0xffffffffu, want);
                 // drop candidates already in the exact list
                 unsigned m2 = mask;
