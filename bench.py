@@ -283,7 +283,7 @@ def main():
             "evals_per_s_fp64": world * fp64["evals"] / (fp64_ms / 1e3),
             "speedup_mixed_vs_fp64": (fp64_ms / max(1, args.fp64_steps)) / (mixed_ms / steps),
             "rounds": info["rounds"], "updates": info["updates"], "fcc_hits": info["fcc_hits"],
-            "rescored_per_build": info["rescored"],
+            "rescored_per_build": info["rescored"], "merge_fallback_rows": info["merge_fallbacks"],
             "phase_ms_per_build": {p: st["phase_ms"][p] / steps for p in st["phase_ms"]},
             "phase_share": phase_share,
             "roofline": {"kernel": "join_mixed_kernel<24,1>", "bound": "alu", "achieved": achieved,

@@ -95,6 +95,7 @@ typedef struct {
     int64_t init_pairs;                      /* pairs scored by the initial graph (n*K) */
     int64_t rescored;                        /* mixed forms: pairs re-scored in FP64 */
     int64_t bound_violations;                /* debug audit: FP32 errors above the bound (must be 0) */
+    int64_t merge_fallbacks;                 /* rows the merge finished on its serial path */
 } knnd_build_info;
 
 /* Phases of the descent, for the per-phase timing of knnd_stats. */

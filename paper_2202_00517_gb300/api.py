@@ -36,7 +36,8 @@ def _info_dict(info: _lib.knnd_build_info) -> dict:
             "updates": [info.updates[i] for i in range(r)],
             "fcc_hits": [info.fcc_hits[i] for i in range(r + 1)],
             "proposals": info.proposals, "init_pairs": info.init_pairs,
-            "rescored": info.rescored, "bound_violations": info.bound_violations}
+            "rescored": info.rescored, "bound_violations": info.bound_violations,
+            "merge_fallbacks": info.merge_fallbacks}
 
 
 class Handle:

@@ -51,7 +51,7 @@ void free_all(knnd_handle *h)
 {
     void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg,
                     h->cof_off, h->cof, h->scan_tmp, h->tau, h->idxK, h->phi, h->Ex, h->bcnt, h->bkey,
-                    h->bidx, h->bent, h->cnt, h->pts_dev, h->idx_dev, h->key_dev};
+                    h->bent, h->fb_list, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->cnt_host) cudaFreeHost(h->cnt_host);
@@ -232,9 +232,10 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     if (!s) s = dalloc(h, &h->phi, n);
     if (!s) s = dalloc(h, &h->Ex, n);
     if (!s) s = dalloc(h, &h->bcnt, n);
-    if (!s && mixed) s = dalloc(h, &h->bent, h->bucket_cap);
+    if (!s) s = dalloc(h, &h->bent, h->bucket_cap);
     if (!s && !mixed) s = dalloc(h, &h->bkey, h->bucket_cap);
-    if (!s && !mixed) s = dalloc(h, &h->bidx, h->bucket_cap);
+    if (!s) s = dalloc(h, &h->fb_list, n);
+    if (!s) s = dalloc(h, &h->fb_count, 1);
     if (!s) s = dalloc(h, &h->cnt, kCntNum);
     if (!s && cudaMallocHost((void **)&h->cnt_host, sizeof(int64_t) * kCntNum) != cudaSuccess) s = KNND_ENOMEM;
     if (!s && prm.timing) {
@@ -367,6 +368,7 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
         info->fcc_hits[r] = hst[kCntHits];
         info->rescored += hst[kCntRescored];
         info->bound_violations += hst[kCntBoundViol];
+        info->merge_fallbacks += hst[kCntFallback];
         info->proposals += per_round;
         info->rounds = r;
         if (info->fcc_hits[r] <= info->fcc_hits[r - 1]) {

@@ -15,10 +15,13 @@
 // K*K + (K+1)*indeg(x), so it cannot overflow): one atomicAdd per (hub, row)
 // reserves the row's slots, then the surviving lanes write consecutively.
 //
-// FP64 form: key in FP64, exact filter (key, y) < (tau_x, idxK_x).
+// FP64 form: key in FP64, exact filter (key, y) < (tau_x, idxK_x); the entry
+// stores the key (bkey) and its FP32 round-up.
 // Mixed form: FP32 dot with FP32 accumulation; the pair is rejected only when
 // dot + E_x < negH_x - tau_x, i.e. when it provably cannot beat the K-th
-// entry (phi_x = that threshold, rounded down); the merge re-scores in FP64.
+// entry (phi_x = that threshold, rounded down); the entry stores -dot and the
+// merge re-scores in FP64.  Either way the entry's first word orders the
+// candidates like their keys (sortable float bits).
 #include <algorithm>
 
 #include "knnd_internal.cuh"
@@ -42,7 +45,6 @@ struct JoinArgs {
     int32_t *bcnt;
     int2 *bent;
     double *bkey;
-    int32_t *bidx;
     int32_t *err;
     int debug;
 };
@@ -201,11 +203,12 @@ __global__ void __launch_bounds__(256) join_mixed_kernel(JoinArgs a)
                 for (int c = 0; c < CPL; ++c) {
                     const unsigned m = __shfl_sync(FULL, mymask[c], rr);
                     if (rb >= 0 && ((m >> lane) & 1u))
-                        a.bent[rb + __popc(m & lt)] = make_int2(__float_as_int(sD[(c * 32 + rr) * 33 + lane]), cid[c]);
+                        a.bent[rb + __popc(m & lt)] =
+                            make_int2((int)sortable_bits(-sD[(c * 32 + rr) * 33 + lane]), cid[c]);
                     rb += __popc(m);
                 }
             }
-            if (cfpass && rowbase >= 0) a.bent[rowbase + count - 1] = make_int2(__float_as_int(cfd), (int)v);
+            if (cfpass && rowbase >= 0) a.bent[rowbase + count - 1] = make_int2((int)sortable_bits(-cfd), (int)v);
             __syncwarp();
         }
         __syncwarp();
@@ -362,15 +365,16 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                     const unsigned m = __shfl_sync(FULL, mymask[c], rr);
                     if (rb >= 0 && ((m >> lane) & 1u)) {
                         const int64_t pos = rb + __popc(m & lt);
-                        a.bkey[pos] = sD[(c * 32 + rr) * 33 + lane];
-                        a.bidx[pos] = cid[c];
+                        const double k = sD[(c * 32 + rr) * 33 + lane];
+                        a.bkey[pos] = k;
+                        a.bent[pos] = make_int2((int)sortable_bits(__double2float_ru(k)), cid[c]);
                     }
                     rb += __popc(m);
                 }
             }
             if (cfpass && rowbase >= 0) {
                 a.bkey[rowbase + count - 1] = cfk;
-                a.bidx[rowbase + count - 1] = (int)v;
+                a.bent[rowbase + count - 1] = make_int2((int)sortable_bits(__double2float_ru(cfk)), (int)v);
             }
             __syncwarp();
         }
@@ -434,7 +438,6 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
     a.bcnt = h->bcnt;
     a.bent = h->bent;
     a.bkey = h->bkey;
-    a.bidx = h->bidx;
     a.err = h->err;
     a.debug = h->prm.debug;
     cudaMemsetAsync(h->bcnt, 0, sizeof(int32_t) * h->n, h->stream);

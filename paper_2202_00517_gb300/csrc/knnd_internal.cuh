@@ -88,6 +88,17 @@ __device__ __forceinline__ bool lex_less(double ka, int ia, double kb, int ib) {
     return ka < kb || (ka == kb && ia < ib);
 }
 
+// Order-preserving 32-bit image of a float: a < b  <=>  sortable(a) < sortable(b)
+// (unsigned), for every non-NaN a, b (-0 sorts just below +0).
+__device__ __forceinline__ uint32_t sortable_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float from_sortable_bits(uint32_t s) {
+    return __uint_as_float((s & 0x80000000u) ? (s & 0x7fffffffu) : ~s);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -105,6 +116,7 @@ enum Counter : int {
     kCntHits = 1,
     kCntRescored = 2,
     kCntBoundViol = 3,
+    kCntFallback = 4,
     kCntNum = 8
 };
 
@@ -140,9 +152,13 @@ struct knnd_handle {
     // buckets
     int32_t *bcnt;  // n
     int64_t bucket_cap;
-    double *bkey;   // FP64 form: bucket keys
-    int32_t *bidx;  // FP64 form: bucket indices
-    int2 *bent;     // mixed form: (FP32 dot bits, index)
+    // bucket entry: (sortable bits of u, index), u a float that orders the
+    // candidates like their keys: mixed form u = -(FP32 dot), FP64 form
+    // u = key rounded up to FP32.  FP64 form: the exact key at the same slot.
+    int2 *bent;
+    double *bkey;
+    int32_t *fb_list;   // n: rows the merge's fast path leaves to the serial path
+    int32_t *fb_count;
     // counters
     int64_t *cnt;       // kCntNum device counters
     int64_t *cnt_host;  // pinned mirror

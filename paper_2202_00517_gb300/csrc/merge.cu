@@ -4,33 +4,62 @@
 // the join appended to its bucket; duplicates and x itself never enter.
 //
 // One warp per point x.  The list lives in registers, entry q = lane + 32*e
-// (e < NE, NE = 1 for K <= 32, 2 for K <= 64).  A candidate that beats the
-// K-th entry is inserted by one ballot (rank), one shuffle-up (shift) and a
-// select; a ballot of index equality rejects duplicates.
+// (e < NE, NE = 1 for K <= 32, 2 for K <= 64); a candidate that beats the K-th
+// entry is inserted by one ballot (rank), one shuffle-up (shift) and a select;
+// a ballot of index equality rejects duplicates.
 //
-// FP64 form: bucket entries carry exact keys.
-// Mixed form: bucket entries carry the FP32 dot d~; the exact key lies in
-// [negH - d~ - E_x, negH - d~ + E_x].  Pass A keeps the K best upper bounds
-// (old entries: exact keys) -> T, an upper bound of the exact K-th key of the
-// whole pool.  Pass B re-scores in FP64 (canonical fma chain) only the
-// candidates whose lower bound is <= T and <= the current exact K-th key and
-// that are not already in the exact list, and inserts them.  The result equals
-// the FP64 form's bit for bit.
+// Every bucket entry already passed the join's filter against the old K-th
+// entry, and its first word orders it like its key (u: mixed form -dot,
+// FP64 form the key rounded up to FP32).  The fast path therefore ranks
+// candidates with integer compares only (GB300's FP64 pipe is narrow):
+//  1. each lane scans its share of the bucket, drops old friends (per-warp
+//     shared-memory hash) and copies of entries it holds, keeps its R smallest
+//     (u, index), and remembers the smallest u it pushed out;
+//  2. T, an upper bound of the exact K-th key of the pool: the old K-th key,
+//     or (when more than 32 candidates pass) the bound of the K-th smallest
+//     distinct (u, index) kept, by K rounds of warp argmin;
+//  3. if some lane pushed out an entry that could still reach T, the row is
+//     listed and finished by a second kernel on the serial path; otherwise the kept entries that can reach
+//     T get their exact key (FP64 form: stored; mixed form: canonical FP64
+//     re-score) and are inserted into the old list one by one.
+// The result equals the FP64 form's bit for bit.
+#include <math_constants.h>
+
 #include <algorithm>
 
 #include "knnd_internal.cuh"
 
 namespace knnd {
 
+// Exact FP64 keys as order-preserving 64-bit integers, so that the list's
+// comparisons run on the integer pipe (GB300's FP64 pipe is narrow).  -0 is
+// mapped to +0 so that equal keys stay equal.
+__device__ __forceinline__ uint64_t dkey(double d)
+{
+    uint64_t b = (uint64_t)__double_as_longlong(d);
+    if (b == 0x8000000000000000ull) b = 0;
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double from_dkey(uint64_t s)
+{
+    return __longlong_as_double((long long)((s & 0x8000000000000000ull) ? (s & 0x7fffffffffffffffull) : ~s));
+}
+
+__device__ __forceinline__ bool lex_less_u(uint64_t ka, int ia, uint64_t kb, int ib)
+{
+    return ka < kb || (ka == kb && ia < ib);
+}
+
 template <int NE>
 struct WarpList {
-    double k[NE];
+    uint64_t k[NE];  // dkey of the exact key
     int i[NE];
     int old[NE];
 
-    __device__ __forceinline__ void kth(int K, double &kk, int &ik) const {
+    __device__ __forceinline__ void kth(int K, uint64_t &kk, int &ik) const {
         const int e = (K - 1) >> 5, src = (K - 1) & 31;
-        double kv = k[0];
+        uint64_t kv = k[0];
         int iv = i[0];
 #pragma unroll
         for (int t = 1; t < NE; ++t)
@@ -48,14 +77,14 @@ struct WarpList {
         return __any_sync(0xffffffffu, f);
     }
     // insert (ck, ci) which is known to be better than the K-th entry and absent
-    __device__ __forceinline__ void insert(int K, int lane, double ck, int ci, int cold) {
+    __device__ __forceinline__ void insert(int K, int lane, uint64_t ck, int ci, int cold) {
         int p = 0;
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
-            const bool less = (lane + 32 * e < K) && lex_less(k[e], i[e], ck, ci);
+            const bool less = (lane + 32 * e < K) && lex_less_u(k[e], i[e], ck, ci);
             p += __popc(__ballot_sync(0xffffffffu, less));
         }
-        double uk[NE];
+        uint64_t uk[NE];
         int ui[NE], uo[NE];
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
@@ -64,16 +93,14 @@ struct WarpList {
             uo[e] = __shfl_up_sync(0xffffffffu, old[e], 1);
         }
 #pragma unroll
-        for (int e = NE - 1; e >= 0; --e) {
-            if (e > 0) {  // lane 0 of slot e takes lane 31 of slot e-1
-                const double ck2 = __shfl_sync(0xffffffffu, k[e - 1], 31);
-                const int ci2 = __shfl_sync(0xffffffffu, i[e - 1], 31);
-                const int co2 = __shfl_sync(0xffffffffu, old[e - 1], 31);
-                if (lane == 0) {
-                    uk[e] = ck2;
-                    ui[e] = ci2;
-                    uo[e] = co2;
-                }
+        for (int e = NE - 1; e >= 1; --e) {  // lane 0 of slot e takes lane 31 of slot e-1
+            const uint64_t ck2 = __shfl_sync(0xffffffffu, k[e - 1], 31);
+            const int ci2 = __shfl_sync(0xffffffffu, i[e - 1], 31);
+            const int co2 = __shfl_sync(0xffffffffu, old[e - 1], 31);
+            if (lane == 0) {
+                uk[e] = ck2;
+                ui[e] = ci2;
+                uo[e] = co2;
             }
         }
 #pragma unroll
@@ -90,6 +117,13 @@ struct WarpList {
             }
         }
     }
+    // insert (ck, ci) if it beats the K-th entry and is not listed yet
+    __device__ __forceinline__ void offer(int K, int lane, uint64_t ck, int ci, uint64_t &kk, int &ik) {
+        if (!lex_less_u(ck, ci, kk, ik)) return;
+        if (contains(K, lane, ci)) return;
+        insert(K, lane, ck, ci, 0);
+        kth(K, kk, ik);
+    }
 };
 
 struct MergeArgs {
@@ -103,13 +137,14 @@ struct MergeArgs {
     const int32_t *bcnt;
     const int2 *bent;
     const double *bkey;
-    const int32_t *bidx;
     const double *X64;
     const double *L64;
     const double *negH;
     const double *Ex;
     int64_t *cnt;
     int32_t *err;
+    int32_t *fb_list;   // rows left to the serial path
+    int32_t *fb_count;
 };
 
 template <int NE>
@@ -121,7 +156,7 @@ __device__ __forceinline__ void write_row(const MergeArgs &a, int64_t x, int lan
         const int q = lane + 32 * e;
         if (q < a.K) {
             a.idx[x * a.K + q] = X.i[e];
-            a.key[x * a.K + q] = X.k[e];
+            a.key[x * a.K + q] = from_dkey(X.k[e]);
             if (a.flag) a.flag[x * a.K + q] = X.old[e] ? 0 : 1;
             newcount += X.old[e] ? 0 : 1;
         }
@@ -135,28 +170,14 @@ __device__ __forceinline__ void load_row(const MergeArgs &a, int64_t x, int lane
     for (int e = 0; e < NE; ++e) {
         const int q = lane + 32 * e;
         if (q < a.K) {
-            X.k[e] = a.key[x * a.K + q];
+            X.k[e] = dkey(a.key[x * a.K + q]);
             X.i[e] = a.idx[x * a.K + q];
         } else {
-            X.k[e] = 0.0;
+            X.k[e] = 0;
             X.i[e] = -1;
         }
         X.old[e] = 1;
     }
-}
-
-// Lane-parallel test of y against the row's original list (indices `oi`, entry
-// q = lane + 32 e): every lane checks its own candidate, K shuffles in all.
-template <int NE>
-__device__ __forceinline__ bool in_old_list(const int (&oi)[NE], int K, int y)
-{
-    bool f = false;
-#pragma unroll
-    for (int e = 0; e < NE; ++e) {
-        const int lim = min(32, K - 32 * e);
-        for (int t = 0; t < lim; ++t) f |= (__shfl_sync(0xffffffffu, oi[e], t) == y);
-    }
-    return f;
 }
 
 // Entries the join wrote for x, never more than the row's capacity.
@@ -171,160 +192,359 @@ __device__ __forceinline__ int bucket_count(const MergeArgs &a, int64_t x)
     return c;
 }
 
-__device__ __forceinline__ void flush_updates(int64_t *cnt, int newcount)
+__device__ __forceinline__ void flush_counts(const MergeArgs &a, int newcount, long long rescored,
+                                             long long fallbacks)
 {
-    for (int o = 16; o > 0; o >>= 1) newcount += __shfl_xor_sync(0xffffffffu, newcount, o);
-    if ((threadIdx.x & 31) == 0 && newcount) atomicAdd((unsigned long long *)&cnt[kCntUpdates], (unsigned long long)newcount);
+    newcount = __reduce_add_sync(0xffffffffu, newcount);
+    for (int o = 16; o > 0; o >>= 1) {
+        rescored += __shfl_xor_sync(0xffffffffu, rescored, o);
+        fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (newcount) atomicAdd((unsigned long long *)&a.cnt[kCntUpdates], (unsigned long long)newcount);
+        if (rescored) atomicAdd((unsigned long long *)&a.cnt[kCntRescored], (unsigned long long)rescored);
+        if (fallbacks) atomicAdd((unsigned long long *)&a.cnt[kCntFallback], (unsigned long long)fallbacks);
+    }
 }
 
-// ------------------------------------------------------------------ FP64 form
-template <int NE>
-__global__ void __launch_bounds__(256) merge_fp64_kernel(MergeArgs a)
+// Canonical FP64 key of (x, y): the same fma chain as the join and the
+// initial graph, with loads issued eight coordinates at a time.
+__device__ __forceinline__ double rescore(const MergeArgs &a, int64_t x, int y, double nh)
 {
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    const int K = a.K;
-    int newcount = 0;
-    for (int64_t x = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); x < a.n; x += (int64_t)gridDim.x * wpb) {
-        WarpList<NE> X;
-        load_row(a, x, lane, X);
-        int oi[NE];
+    const double2 *xr = reinterpret_cast<const double2 *>(a.X64 + x * a.MP);
+    const double2 *lr = reinterpret_cast<const double2 *>(a.L64 + (int64_t)y * a.MP);
+    double acc = 0.0;
+    for (int i8 = 0; i8 < a.MP / 8; ++i8) {
+        double2 p[4], q[4];
 #pragma unroll
-        for (int e = 0; e < NE; ++e) oi[e] = X.i[e];
-        double tk;
+        for (int t = 0; t < 4; ++t) {
+            p[t] = __ldg(xr + 4 * i8 + t);
+            q[t] = __ldg(lr + 4 * i8 + t);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            acc = __fma_rn(p[t].x, q[t].x, acc);
+            acc = __fma_rn(p[t].y, q[t].y, acc);
+        }
+    }
+    return nh - acc;
+}
+
+// ------------------------------------------------------------------ old-list set
+// Per-warp open-addressing set of the row's old friend indices in shared
+// memory (kHashSlots >= 2 K): about one probe per lookup.
+constexpr int kHashSlots = 128;
+
+__device__ __forceinline__ unsigned hash_slot(int y) { return ((unsigned)y * 0x9E3779B1u) >> 25; }
+
+template <int NE>
+__device__ __forceinline__ void hash_fill(int *tab, int lane, int K, const WarpList<NE> &X)
+{
+    for (int s = lane; s < kHashSlots; s += 32) tab[s] = -1;
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+        const int y = X.i[e];
+        if (lane + 32 * e < K && y >= 0) {
+            unsigned sl = hash_slot(y);
+            for (int t = 0; t < kHashSlots; ++t) {
+                const int prev = atomicCAS(&tab[sl], -1, y);
+                if (prev == -1 || prev == y) break;
+                sl = (sl + 1) & (kHashSlots - 1);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool hash_has(const int *tab, int y)
+{
+    unsigned sl = hash_slot(y);
+    for (int t = 0; t < kHashSlots; ++t) {
+        const int v = tab[sl];
+        if (v == y) return true;
+        if (v == -1) return false;
+        sl = (sl + 1) & (kHashSlots - 1);
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ key bounds
+// Bounds of the exact key of an entry from its u, and the u-threshold of
+// "lower bound <= T".
+template <bool MIXED>
+struct Bounds {
+    double nh, E;
+    __device__ __forceinline__ double upper(float u) const { return MIXED ? (nh + (double)u) + E : (double)u; }
+    // every entry whose lower bound is <= T has u <= u_reach(T)
+    __device__ __forceinline__ float u_reach(double T) const {
+        return MIXED ? __double2float_ru((T - nh) + E) : __double2float_ru(T);
+    }
+};
+
+// ------------------------------------------------------------------ serial path
+// Candidates are inserted one at a time.  Used for rows the fast path cannot
+// settle.  Mixed form: pass A keeps the K best upper bounds (threshold T),
+// pass B re-scores every candidate whose lower bound reaches T.
+template <int NE, bool MIXED>
+__device__ void serial_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &X, const int *tab, int64_t base,
+                           int cnt, const Bounds<MIXED> &B, long long &rescored)
+{
+    const int K = a.K;
+    double T = CUDART_INF;
+    if (MIXED) {
+        WarpList<NE> A = X;
+        uint64_t tk;
         int ti;
-        X.kth(K, tk, ti);
-        const int64_t base = (int64_t)K * K * x + (int64_t)(K + 1) * a.cof_off[x];
-        const int cnt = bucket_count(a, x);
+        A.kth(K, tk, ti);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             const bool has = c0 + lane < cnt;
-            double ck = 0.0;
+            uint64_t ub = ~0ull;
             int ci = -1;
             if (has) {
-                ck = a.bkey[base + c0 + lane];
-                ci = a.bidx[base + c0 + lane];
+                const int2 en = a.bent[base + c0 + lane];
+                ub = dkey(B.upper(from_sortable_bits((uint32_t)en.x)));
+                ci = en.y;
             }
-            const bool old = in_old_list(oi, K, ci);
-            unsigned mask = __ballot_sync(0xffffffffu, has && !old && lex_less(ck, ci, tk, ti));
+            const bool take = has && ci >= 0 && ci < a.n && !hash_has(tab, ci);
+            unsigned mask = __ballot_sync(0xffffffffu, take && lex_less_u(ub, ci, tk, ti));
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const double k1 = __shfl_sync(0xffffffffu, ck, src);
-                const int i1 = __shfl_sync(0xffffffffu, ci, src);
-                if (!lex_less(k1, i1, tk, ti)) continue;
-                if (X.contains(K, lane, i1)) continue;
-                X.insert(K, lane, k1, i1, 0);
-                X.kth(K, tk, ti);
+                A.offer(K, lane, __shfl_sync(0xffffffffu, ub, src), __shfl_sync(0xffffffffu, ci, src), tk, ti);
             }
         }
-        write_row(a, x, lane, X, newcount);
+        T = from_dkey(tk);
     }
-    flush_updates(a.cnt, newcount);
+    uint64_t xk;
+    int xi;
+    X.kth(K, xk, xi);
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const bool has = c0 + lane < cnt;
+        int ci = -1;
+        float u = 0.f;
+        if (has) {
+            const int2 en = a.bent[base + c0 + lane];
+            u = from_sortable_bits((uint32_t)en.x);
+            ci = en.y;
+        }
+        bool want = has && ci >= 0 && ci < a.n && !hash_has(tab, ci);
+        if (MIXED) want = want && u <= B.u_reach(fmin(T, from_dkey(xk)));
+        uint64_t k = 0;
+        if (want) {
+            if (MIXED) {
+                k = dkey(rescore(a, x, ci, B.nh));
+                rescored += 1;
+            } else {
+                k = dkey(a.bkey[base + c0 + lane]);
+            }
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, want);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            X.offer(K, lane, __shfl_sync(0xffffffffu, k, src), __shfl_sync(0xffffffffu, ci, src), xk, xi);
+        }
+    }
 }
 
-// ------------------------------------------------------------------ mixed form
-template <int NE>
-__global__ void __launch_bounds__(256) merge_mixed_kernel(MergeArgs a)
+// ------------------------------------------------------------------ fast path
+template <int R>
+struct LaneTop {
+    uint64_t pk[R];   // (sortable u << 32) | index, ascending; ~0 = empty
+    int pos[R];       // bucket slot of the entry
+    uint32_t drop;    // smallest sortable u pushed out (~0 = none)
+
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            pk[r] = ~0ull;
+            pos[r] = 0;
+        }
+        drop = 0xffffffffu;
+    }
+    __device__ __forceinline__ void push(uint64_t p, int ps) {
+        if (p >= pk[R - 1]) {
+            drop = min(drop, (uint32_t)(p >> 32));
+            return;
+        }
+        // a copy of an entry this lane already holds (same index, same u) adds nothing
+        bool dup = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dup |= (pk[r] == p);
+        if (dup) return;
+        if (pk[R - 1] != ~0ull) drop = min(drop, (uint32_t)(pk[R - 1] >> 32));
+        bool placed = false;
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) {
+            if (placed) continue;
+            if (r > 0 && p < pk[r - 1]) {
+                pk[r] = pk[r - 1];
+                pos[r] = pos[r - 1];
+            } else {
+                pk[r] = p;
+                pos[r] = ps;
+                placed = true;
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v)
 {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t < v ? t : v;
+    }
+    return v;
+}
+
+template <int NE, int R, bool MIXED>
+__device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &X, const int *tab, int2 *live_list,
+                         int64_t base, int cnt, const Bounds<MIXED> &B, long long &rescored)
+{
+    const int K = a.K;
+    LaneTop<R> L;
+    L.init();
+    int passing = 0;
+    for (int c0 = lane; c0 < cnt; c0 += 4 * 32) {
+        int2 en[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)  // four independent loads in flight per lane
+            en[t] = (c0 + 32 * t < cnt) ? a.bent[base + c0 + 32 * t] : make_int2(0, -1);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (en[t].y < 0 || en[t].y >= a.n || hash_has(tab, en[t].y)) continue;
+            passing += 1;
+            L.push(((uint64_t)(uint32_t)en[t].x << 32) | (uint32_t)en[t].y, c0 + 32 * t);
+        }
+    }
+    const int P = __reduce_add_sync(0xffffffffu, passing);
+    if (P == 0) return true;
+    uint64_t T0;
+    int Ti;
+    X.kth(K, T0, Ti);
+    double T = from_dkey(T0);
+    if (P > 32) {
+        int popped = 0, count = 0;
+        uint64_t prev = ~0ull, m = ~0ull;
+        while (count < K) {
+            uint64_t head = ~0ull;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (r == popped) head = L.pk[r];
+            m = warp_min_u64(head);
+            if (m == ~0ull) break;
+            const int win = __ffs(__ballot_sync(0xffffffffu, head == m)) - 1;
+            if (lane == win) popped += 1;
+            if (m == prev) continue;
+            prev = m;
+            count += 1;
+        }
+        if (count == K) T = fmin(T, B.upper(from_sortable_bits((uint32_t)(m >> 32))));
+    }
+    const uint32_t reach = sortable_bits(B.u_reach(T));
+    if (__any_sync(0xffffffffu, L.drop <= reach)) return false;
+    // compact the entries that can reach T, then key them 32 at a time
+    const unsigned lt = lanemask_lt();
+    int nlive = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool live = L.pk[r] != ~0ull && (uint32_t)(L.pk[r] >> 32) <= reach;
+        const unsigned mask = __ballot_sync(0xffffffffu, live);
+        if (live) live_list[nlive + __popc(mask & lt)] = make_int2((int)(uint32_t)L.pk[r], L.pos[r]);
+        nlive += __popc(mask);
+    }
+    __syncwarp();
+    uint64_t xk;
+    int xi;
+    X.kth(K, xk, xi);
+    for (int c0 = 0; c0 < nlive; c0 += 32) {
+        const bool has = c0 + lane < nlive;
+        int ci = -1;
+        uint64_t k = ~0ull;
+        if (has) {
+            const int2 e = live_list[c0 + lane];
+            ci = e.x;
+            if (MIXED) {
+                k = dkey(rescore(a, x, ci, B.nh));
+                rescored += 1;
+            } else {
+                k = dkey(a.bkey[base + e.y]);
+            }
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, has);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            X.offer(K, lane, __shfl_sync(0xffffffffu, k, src), __shfl_sync(0xffffffffu, ci, src), xk, xi);
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+template <int NE, int R, bool MIXED>
+__global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
+{
+    __shared__ int s_hash[8][kHashSlots];
+    __shared__ int2 s_live[8][32 * R];
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int K = a.K;
-    const int MP = a.MP;
+    int *tab = s_hash[threadIdx.x >> 5];
+    int2 *live_list = s_live[threadIdx.x >> 5];
     int newcount = 0;
-    long long rescored = 0;
+    long long rescored = 0, fallbacks = 0;
     for (int64_t x = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); x < a.n; x += (int64_t)gridDim.x * wpb) {
         WarpList<NE> X;
         load_row(a, x, lane, X);
-        int oi[NE];
-#pragma unroll
-        for (int e = 0; e < NE; ++e) oi[e] = X.i[e];
         const int64_t base = (int64_t)K * K * x + (int64_t)(K + 1) * a.cof_off[x];
         const int cnt = bucket_count(a, x);
         if (cnt > 0) {
-            const double nh = a.negH[x];
-            const double E = a.Ex[x];
-            // pass A: K best upper bounds
-            WarpList<NE> A = X;
-            double tk, xk;
-            int ti, xi;
-            A.kth(K, tk, ti);
-            for (int c0 = 0; c0 < cnt; c0 += 32) {
-                const bool has = c0 + lane < cnt;
-                double ub = 0.0;
-                int ci = -1;
-                if (has) {
-                    const int2 en = a.bent[base + c0 + lane];
-                    ub = (nh - (double)__int_as_float(en.x)) + E;
-                    ci = en.y;
-                }
-                // old friends re-proposed by the join are dropped without serial work
-                const bool old = in_old_list(oi, K, ci);
-                unsigned mask = __ballot_sync(0xffffffffu, has && !old && lex_less(ub, ci, tk, ti));
-                while (mask) {
-                    const int src = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const double k1 = __shfl_sync(0xffffffffu, ub, src);
-                    const int i1 = __shfl_sync(0xffffffffu, ci, src);
-                    if (!lex_less(k1, i1, tk, ti)) continue;
-                    if (A.contains(K, lane, i1)) continue;
-                    A.insert(K, lane, k1, i1, 0);
-                    A.kth(K, tk, ti);
-                }
-            }
-            const double T = tk;
-            // pass B: exact re-score of the candidates the bounds cannot reject
-            X.kth(K, xk, xi);
-            for (int c0 = 0; c0 < cnt; c0 += 32) {
-                const bool has = c0 + lane < cnt;
-                double lb = 0.0;
-                int ci = -1;
-                if (has) {
-                    const int2 en = a.bent[base + c0 + lane];
-                    lb = (nh - (double)__int_as_float(en.x)) - E;
-                    ci = en.y;
-                }
-                const bool old = in_old_list(oi, K, ci);  // warp-collective: every lane calls it
-                bool want = has && !old && lb <= T && lb <= xk && ci >= 0 && ci < a.n;
-                unsigned mask = __ballot_sync(0xffffffffu, want);
-                // drop candidates already in the exact list
-                unsigned m2 = mask;
-                while (m2) {
-                    const int src = __ffs(m2) - 1;
-                    m2 &= m2 - 1;
-                    const int i1 = __shfl_sync(0xffffffffu, ci, src);
-                    if (X.contains(K, lane, i1) && lane == src) want = false;
-                }
-                double kex = 0.0;
-                if (want) {
-                    const double2 *xr = reinterpret_cast<const double2 *>(a.X64 + x * MP);
-                    const double2 *lr = reinterpret_cast<const double2 *>(a.L64 + (int64_t)ci * MP);
-                    double acc = 0.0;
-                    for (int i2 = 0; i2 < MP / 2; ++i2) {
-                        const double2 p = __ldg(xr + i2), q = __ldg(lr + i2);
-                        acc = __fma_rn(p.x, q.x, acc);
-                        acc = __fma_rn(p.y, q.y, acc);
-                    }
-                    kex = nh - acc;
-                    rescored += 1;
-                }
-                mask = __ballot_sync(0xffffffffu, want);
-                while (mask) {
-                    const int src = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const double k1 = __shfl_sync(0xffffffffu, kex, src);
-                    const int i1 = __shfl_sync(0xffffffffu, ci, src);
-                    if (!lex_less(k1, i1, xk, xi)) continue;
-                    if (X.contains(K, lane, i1)) continue;
-                    X.insert(K, lane, k1, i1, 0);
-                    X.kth(K, xk, xi);
-                }
+            Bounds<MIXED> B;
+            B.nh = MIXED ? a.negH[x] : 0.0;
+            B.E = MIXED ? a.Ex[x] : 0.0;
+            hash_fill(tab, lane, K, X);
+            if (!fast_row<NE, R, MIXED>(a, x, lane, X, tab, live_list, base, cnt, B, rescored)) {
+                // the row stays as it is here; merge_fallback_kernel finishes it
+                if (lane == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)x;
+                fallbacks += 1;
+                continue;
             }
         }
         write_row(a, x, lane, X, newcount);
     }
-    flush_updates(a.cnt, newcount);
-    for (int o = 16; o > 0; o >>= 1) rescored += __shfl_xor_sync(0xffffffffu, rescored, o);
-    if (lane == 0 && rescored) atomicAdd((unsigned long long *)&a.cnt[kCntRescored], (unsigned long long)rescored);
+    flush_counts(a, newcount, rescored, fallbacks);
+}
+
+// Rows the fast path could not settle, one warp each, on the serial path.
+template <int NE, bool MIXED>
+__global__ void __launch_bounds__(256) merge_fallback_kernel(MergeArgs a)
+{
+    __shared__ int s_hash[8][kHashSlots];
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int K = a.K;
+    int *tab = s_hash[threadIdx.x >> 5];
+    int newcount = 0;
+    long long rescored = 0;
+    const int nfb = *a.fb_count;
+    for (int f = blockIdx.x * wpb + (threadIdx.x >> 5); f < nfb; f += gridDim.x * wpb) {
+        const int64_t x = a.fb_list[f];
+        WarpList<NE> X;
+        load_row(a, x, lane, X);
+        const int64_t base = (int64_t)K * K * x + (int64_t)(K + 1) * a.cof_off[x];
+        const int cnt = bucket_count(a, x);
+        Bounds<MIXED> B;
+        B.nh = MIXED ? a.negH[x] : 0.0;
+        B.E = MIXED ? a.Ex[x] : 0.0;
+        hash_fill(tab, lane, K, X);
+        serial_row<NE, MIXED>(a, x, lane, X, tab, base, cnt, B, rescored);
+        write_row(a, x, lane, X, newcount);
+    }
+    flush_counts(a, newcount, rescored, 0);
 }
 
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag)
@@ -340,7 +560,6 @@ cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *new
     a.bcnt = h->bcnt;
     a.bent = h->bent;
     a.bkey = h->bkey;
-    a.bidx = h->bidx;
     a.X64 = h->X64;
     a.L64 = h->L64;
     a.negH = h->negH;
@@ -350,15 +569,29 @@ cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *new
     const int threads = 256;
     const int64_t need = (h->n + threads / 32 - 1) / (threads / 32);
     const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * 8);
+    a.fb_list = h->fb_list;
+    a.fb_count = h->fb_count;
+    cudaMemsetAsync(h->fb_count, 0, sizeof(int32_t), h->stream);
     const bool fp64 = h->prec == KNND_PREC_FP64;
+    const unsigned fgrid = (unsigned)h->num_sms * 2;
     if (h->K <= 32) {
-        if (fp64) merge_fp64_kernel<1><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-        else merge_mixed_kernel<1><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+        if (fp64) {
+            merge_kernel<1, 4, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<1, false><<<fgrid, threads, 0, h->stream>>>(a);
+        } else {
+            merge_kernel<1, 4, true><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<1, true><<<fgrid, threads, 0, h->stream>>>(a);
+        }
     } else {
-        if (fp64) merge_fp64_kernel<2><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-        else merge_mixed_kernel<2><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+        if (fp64) {
+            merge_kernel<2, 8, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<2, false><<<fgrid, threads, 0, h->stream>>>(a);
+        } else {
+            merge_kernel<2, 8, true><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<2, true><<<fgrid, threads, 0, h->stream>>>(a);
+        }
     }
-    h->launches += 1;
+    h->launches += 2;
     return cudaGetLastError();
 }
 
