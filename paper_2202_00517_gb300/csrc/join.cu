@@ -52,62 +52,86 @@ struct JoinArgs {
 __device__ __forceinline__ bool valid_id(int64_t v, int64_t n) { return v >= 0 && v < n; }
 
 // ------------------------------------------------------------------ mixed
-template <int MP, int CPL>
+// Lane (g, p): column pair p (columns 2p, 2p+1; their FP32 log rows live in
+// registers) of row group g; a pass scores two rows per group, 2 x G rows in
+// all (G = 32 / ceil(K/2) groups; K = 20: 30 lanes busy, six rows a pass).
+// Each lane reuses every coordinate it reads from shared memory for two
+// columns.  The dots go to shared memory; then lane t owns row t of the chunk:
+// it applies the filter, scores the co-friend pair (rows of F(v)), reserves the
+// row's slots with one atomicAdd and writes its survivors.
+template <int MP>
 struct MixedSmem {
-    static constexpr int RS = MP + 4;  // row stride in floats (16-byte aligned, conflict-free float4 phases)
-    static constexpr int X_FLOATS = 33 * RS;
-    static constexpr int D_FLOATS = CPL * 32 * 33;
-    static constexpr int WARP_FLOATS = X_FLOATS + D_FLOATS;
+    static constexpr int RS = MP + 4;       // row stride of the staged coordinates (floats)
+    static constexpr int X_FLOATS = 33 * RS; // 32 rows + the hub's own log row
+    // dots of one row: stride K or K+1, whichever is odd (conflict-free row reads)
+    static __host__ __device__ int d_stride(int K) { return (K & 1) ? K : K + 1; }
+    // per warp: coordinates | dots | column ids (64) | survivor columns (32 x K bytes)
+    //           | survivor prefix (32 ints) | row bases (32 int64)
+    static __host__ __device__ int off_cid(int K) { return 4 * (X_FLOATS + 32 * d_stride(K)); }
+    static __host__ __device__ int off_j(int K) { return off_cid(K) + 4 * 64; }
+    static __host__ __device__ int off_inc(int K) { return off_j(K) + ((32 * K + 15) & ~15); }
+    static __host__ __device__ int off_rb(int K) { return off_inc(K) + 4 * 32; }
+    static __host__ __device__ int warp_bytes(int K) { return off_rb(K) + 8 * 32; }
 };
 
-template <int MP, int CPL>
-__global__ void __launch_bounds__(256) join_mixed_kernel(JoinArgs a)
+template <int MP>
+__global__ void __launch_bounds__(256, (MP <= 32 ? 3 : 1)) join_mixed_kernel(JoinArgs a)
 {
-    using S = MixedSmem<MP, CPL>;
+    using S = MixedSmem<MP>;
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    float *sX = reinterpret_cast<float *>(smem4) + warp * S::WARP_FLOATS;
-    float *sD = sX + S::X_FLOATS;
     const int K = a.K;
+    const int DS = S::d_stride(K);
+    unsigned char *wbase = reinterpret_cast<unsigned char *>(smem4) + (size_t)warp * S::warp_bytes(K);
+    float *sX = reinterpret_cast<float *>(wbase);
+    float *sD = sX + S::X_FLOATS;
+    int *sCid = reinterpret_cast<int *>(wbase + S::off_cid(K));
+    unsigned char *sJ = wbase + S::off_j(K);
+    int *sInc = reinterpret_cast<int *>(wbase + S::off_inc(K));
+    int64_t *sRB = reinterpret_cast<int64_t *>(wbase + S::off_rb(K));
     const int64_t n = a.n;
-    const unsigned FULL = 0xffffffffu;
+    const int npairs = (K + 1) >> 1;
+    const int G = 32 / npairs;                 // row groups
+    const int g = lane / npairs, pr = lane - g * npairs;
+    const bool active = g < G;
+    const int cA = 2 * pr, cB = 2 * pr + 1;     // this lane's columns
 
     for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
-        // columns: F(v), lane j <-> column j (+32 per extra column slot)
-        int cid[CPL];
-        float Lc[CPL][MP];
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int j = lane + 32 * c;
-            int id = -1;
-            if (j < K) {
-                id = a.idx[v * K + j];
-                if (!valid_id(id, n)) {
-                    atomicOr(a.err, kErrIndex);
-                    id = -1;
-                }
+        // column ids of F(v)
+        for (int j = lane; j < K; j += 32) {
+            int id = a.idx[v * K + j];
+            if (!valid_id(id, n)) {
+                atomicOr(a.err, kErrIndex);
+                id = -1;
             }
-            cid[c] = id;
-            const float4 *lr = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(id < 0 ? 0 : id) * MP);
-#pragma unroll
-            for (int i4 = 0; i4 < MP / 4; ++i4) {
-                float4 t = (id >= 0) ? __ldg(lr + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
-                Lc[c][4 * i4 + 0] = t.x;
-                Lc[c][4 * i4 + 1] = t.y;
-                Lc[c][4 * i4 + 2] = t.z;
-                Lc[c][4 * i4 + 3] = t.w;
-            }
+            sCid[j] = id;
         }
-        // the hub's own log row: column v of the co-friend pairs, staged in row slot 32
+        // the hub's own log row: column v of the co-friend pairs, row slot 32
         for (int i4 = lane; i4 < MP / 4; i4 += 32)
             reinterpret_cast<float4 *>(sX + 32 * S::RS)[i4] =
                 __ldg(reinterpret_cast<const float4 *>(a.L32 + v * MP) + i4);
+        __syncwarp();
+        const int idA = (active && cA < K) ? sCid[cA] : -1;
+        const int idB = (active && cB < K) ? sCid[cB] : -1;
+        float LA[MP], LB[MP];
+        {
+            const float4 *ra = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(idA < 0 ? 0 : idA) * MP);
+            const float4 *rb = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(idB < 0 ? 0 : idB) * MP);
+#pragma unroll
+            for (int i4 = 0; i4 < MP / 4; ++i4) {
+                const float4 ta = (idA >= 0) ? __ldg(ra + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 tb = (idB >= 0) ? __ldg(rb + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                LA[4 * i4 + 0] = ta.x; LA[4 * i4 + 1] = ta.y; LA[4 * i4 + 2] = ta.z; LA[4 * i4 + 3] = ta.w;
+                LB[4 * i4 + 0] = tb.x; LB[4 * i4 + 1] = tb.y; LB[4 * i4 + 2] = tb.z; LB[4 * i4 + 3] = tb.w;
+            }
+        }
 
         const int64_t c0 = a.cof_off[v];
         const int64_t nrows = (int64_t)K + (a.cof_off[v + 1] - c0);
         for (int64_t base = 0; base < nrows; base += 32) {
             const int nr = (int)min((int64_t)32, nrows - base);
+            // stage: lane t <-> row t of the chunk
             const int64_t r = base + lane;
             int rid = -1;
             if (r < nrows) {
@@ -131,37 +155,52 @@ __global__ void __launch_bounds__(256) join_mixed_kernel(JoinArgs a)
                 for (int i4 = 0; i4 < MP / 4; ++i4) srow[i4] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncwarp();
-
-            unsigned mymask[CPL];
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) mymask[c] = 0u;
-            for (int rr = 0; rr < nr; ++rr) {
-                const int rrid = __shfl_sync(FULL, rid, rr);
-                const float rph = __shfl_sync(FULL, ph, rr);
-                const float4 *xr = reinterpret_cast<const float4 *>(sX + rr * S::RS);
-                float acc[CPL];
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) acc[c] = 0.f;
+            // score: group g takes rows it*2G + 2g and +1
+            for (int r0 = 2 * g; r0 < nr; r0 += 2 * G) {
+                if (!active) break;
+                const int r1 = r0 + 1;  // row 32 of sX is the hub row: harmless when r1 == nr
+                const float4 *x0 = reinterpret_cast<const float4 *>(sX + r0 * S::RS);
+                const float4 *x1 = reinterpret_cast<const float4 *>(sX + r1 * S::RS);
+                float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
 #pragma unroll
                 for (int i4 = 0; i4 < MP / 4; ++i4) {
-                    const float4 xv = xr[i4];
-#pragma unroll
-                    for (int c = 0; c < CPL; ++c) {
-                        acc[c] = __fmaf_rn(xv.x, Lc[c][4 * i4 + 0], acc[c]);
-                        acc[c] = __fmaf_rn(xv.y, Lc[c][4 * i4 + 1], acc[c]);
-                        acc[c] = __fmaf_rn(xv.z, Lc[c][4 * i4 + 2], acc[c]);
-                        acc[c] = __fmaf_rn(xv.w, Lc[c][4 * i4 + 3], acc[c]);
-                    }
+                    const float4 u = x0[i4], w = x1[i4];
+                    a0 = __fmaf_rn(u.x, LA[4 * i4 + 0], a0); a1 = __fmaf_rn(w.x, LA[4 * i4 + 0], a1);
+                    b0 = __fmaf_rn(u.x, LB[4 * i4 + 0], b0); b1 = __fmaf_rn(w.x, LB[4 * i4 + 0], b1);
+                    a0 = __fmaf_rn(u.y, LA[4 * i4 + 1], a0); a1 = __fmaf_rn(w.y, LA[4 * i4 + 1], a1);
+                    b0 = __fmaf_rn(u.y, LB[4 * i4 + 1], b0); b1 = __fmaf_rn(w.y, LB[4 * i4 + 1], b1);
+                    a0 = __fmaf_rn(u.z, LA[4 * i4 + 2], a0); a1 = __fmaf_rn(w.z, LA[4 * i4 + 2], a1);
+                    b0 = __fmaf_rn(u.z, LB[4 * i4 + 2], b0); b1 = __fmaf_rn(w.z, LB[4 * i4 + 2], b1);
+                    a0 = __fmaf_rn(u.w, LA[4 * i4 + 3], a0); a1 = __fmaf_rn(w.w, LA[4 * i4 + 3], a1);
+                    b0 = __fmaf_rn(u.w, LB[4 * i4 + 3], b0); b1 = __fmaf_rn(w.w, LB[4 * i4 + 3], b1);
                 }
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                    const bool pass = rrid >= 0 && cid[c] >= 0 && cid[c] != rrid && acc[c] >= rph;
-                    const unsigned m = __ballot_sync(FULL, pass);
-                    if (lane == rr) mymask[c] = m;
-                    sD[(c * 32 + rr) * 33 + lane] = acc[c];
+                if (cA < K) {
+                    sD[r0 * DS + cA] = a0;
+                    if (r1 < nr) sD[r1 * DS + cA] = a1;
+                }
+                if (cB < K) {
+                    sD[r0 * DS + cB] = b0;
+                    if (r1 < nr) sD[r1 * DS + cB] = b1;
                 }
             }
-            // co-friend pair (x in F(v), y = v): the row's own lane scores it
+            __syncwarp();
+            // filter: lane t <-> row t; survivors compacted in place in the row's dots,
+            // their column numbers in sJ
+            int q = 0;
+            if (lane < nr && rid >= 0) {
+                float *drow = sD + lane * DS;
+                unsigned char *jrow = sJ + lane * K;
+                for (int j = 0; j < K; ++j) {
+                    const float d = drow[j];
+                    const int cj = sCid[j];
+                    if (cj >= 0 && cj != rid && d >= ph) {
+                        drow[q] = d;
+                        jrow[q] = (unsigned char)j;
+                        ++q;
+                    }
+                }
+            }
+            // co-friend pair (x in F(v), y = v)
             bool cfpass = false;
             float cfd = 0.f;
             if (r < K && rid >= 0) {
@@ -179,10 +218,8 @@ __global__ void __launch_bounds__(256) join_mixed_kernel(JoinArgs a)
                 cfd = acc;
                 cfpass = acc >= ph;
             }
-            int count = cfpass ? 1 : 0;
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) count += __popc(mymask[c]);
-            int64_t rowbase = 0;
+            const int count = q + (cfpass ? 1 : 0);
+            int64_t rowbase = -1;
             if (count > 0) {
                 const int p = atomicAdd(&a.bcnt[rid], count);
                 rowbase = roff + p;
@@ -190,25 +227,37 @@ __global__ void __launch_bounds__(256) join_mixed_kernel(JoinArgs a)
                     const int64_t cap = (int64_t)K * K + (int64_t)(K + 1) * (a.cof_off[rid + 1] - a.cof_off[rid]);
                     if (p + count > cap) {
                         atomicOr(a.err, kErrBucket);
-                        count = 0;
-                        cfpass = false;
                         rowbase = -1;
                     }
                 }
+                if (cfpass && rowbase >= 0) a.bent[rowbase + q] = make_int2((int)sortable_bits(-cfd), (int)v);
             }
-            const unsigned lt = lanemask_lt();
-            for (int rr = 0; rr < nr; ++rr) {
-                int64_t rb = __shfl_sync(FULL, rowbase, rr);
+            // coalesced writes of the column survivors: entry k of the chunk's
+            // flattened list goes to row t = the first with prefix > k
+            int incl = q;
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                    const unsigned m = __shfl_sync(FULL, mymask[c], rr);
-                    if (rb >= 0 && ((m >> lane) & 1u))
-                        a.bent[rb + __popc(m & lt)] =
-                            make_int2((int)sortable_bits(-sD[(c * 32 + rr) * 33 + lane]), cid[c]);
-                    rb += __popc(m);
-                }
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
             }
-            if (cfpass && rowbase >= 0) a.bent[rowbase + count - 1] = make_int2((int)sortable_bits(-cfd), (int)v);
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            sInc[lane] = incl;
+            sRB[lane] = rowbase;
+            __syncwarp();
+            for (int k = lane; k < total; k += 32) {
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int it = 0; it < 5; ++it) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sInc[mid] > k) hi = mid;
+                    else lo = mid + 1;
+                }
+                const int t = lo;
+                const int qq = k - (t ? sInc[t - 1] : 0);
+                const int64_t rb = sRB[t];
+                if (rb >= 0)
+                    a.bent[rb + qq] = make_int2((int)sortable_bits(-sD[t * DS + qq]), sCid[sJ[t * K + qq]]);
+            }
             __syncwarp();
         }
         __syncwarp();
@@ -398,16 +447,16 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * per_sm);
         join_fp64_kernel<MP, CPL><<<(unsigned)grid, threads, smem, h->stream>>>(a);
     } else {
-        using S = MixedSmem<MP, CPL>;
+        using S = MixedSmem<MP>;
         const int threads = 256;
-        const size_t smem = sizeof(float) * S::WARP_FLOATS * (threads / 32);
-        cudaFuncSetAttribute(join_mixed_kernel<MP, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t smem = (size_t)S::warp_bytes(h->K) * (threads / 32);
+        cudaFuncSetAttribute(join_mixed_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_mixed_kernel<MP, CPL>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_mixed_kernel<MP>, threads, smem);
         if (per_sm < 1) per_sm = 1;
         const int64_t need = (h->n + threads / 32 - 1) / (threads / 32);
         const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * per_sm);
-        join_mixed_kernel<MP, CPL><<<(unsigned)grid, threads, smem, h->stream>>>(a);
+        join_mixed_kernel<MP><<<(unsigned)grid, threads, smem, h->stream>>>(a);
     }
     return cudaGetLastError();
 }
