@@ -219,6 +219,52 @@ knnd_status knnd_fcc_noalloc(const int32_t *idx, int64_t n, int32_t K, uint64_t 
  * here instead. */
 knnd_status knnd_sync(knnd_handle *h);
 
+/* ---- batched form --------------------------------------------------------
+ * Many independent instances built together (the same method, per instance,
+ * as knnd_build).  Instances with equal (m, K) share kernel launches: each
+ * phase is one launch over all of them; a class too large for the workspace
+ * budget is cut into sub-batches run one after the other.  Every instance gets
+ * the graph, rounds and counts a separate knnd_build with its seed would give. */
+typedef struct {
+    const void *points; /* device: n x m, row stride ld elements, dtype of the call */
+    int64_t ld;
+    int64_t n;          /* 3 <= n < 2^31 */
+    int32_t m;          /* 1 <= m <= KNND_MAX_M */
+    int32_t K;          /* 2 <= K <= min(n-1, KNND_MAX_K) */
+    uint64_t seed;
+    int32_t *idx;       /* out: device n x K, indices local to the instance */
+    double *key;        /* out: device n x K */
+} knnd_instance;
+
+typedef struct knnd_batch knnd_batch;
+
+/* Plan the sub-batches of `count` instances (the array is copied; the points
+ * and output pointers must stay valid until knnd_batch_run returns) and
+ * allocate one workspace for the largest of them.  workspace_limit: device
+ * bytes a sub-batch may plan for (<= 0: 32 GiB).  Errors: EINVAL (a bad
+ * instance or parameter), ENOMEM, ECUDA. */
+knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instance *inst, knnd_dtype dtype,
+                              knnd_precision precision, const knnd_params *params, int64_t workspace_limit,
+                              void *stream);
+
+/* Build every instance (Sec. 3: initial graph, rounds to the statistical
+ * stop, per instance).  info: host array of `count` reports, or NULL.
+ * Synchronises the stream once per round of each sub-batch.
+ * Errors: EDOMAIN, EINVAL (bad index met on the device), ECUDA. */
+knnd_status knnd_batch_run(knnd_batch *b, knnd_build_info *info);
+
+/* Sub-batches planned, workspace bytes, kernels launched so far (each NULL-able). */
+knnd_status knnd_batch_info(const knnd_batch *b, int32_t *sub_batches, int64_t *workspace_bytes,
+                            int64_t *kernel_launches);
+
+/* Release the batch and its workspace (synchronises its stream).  NULL is a no-op. */
+void knnd_batch_destroy(knnd_batch *b);
+
+/* knnd_batch_create + knnd_batch_run + knnd_batch_destroy. */
+knnd_status knnd_build_batched(int32_t count, const knnd_instance *inst, knnd_dtype dtype,
+                               knnd_precision precision, const knnd_params *params, int64_t workspace_limit,
+                               knnd_build_info *info, void *stream);
+
 /* Counters of the handle (host struct).  Synchronises the stream when
  * timing is on, to read the pending phase events. */
 knnd_status knnd_get_stats(knnd_handle *h, knnd_stats *stats);

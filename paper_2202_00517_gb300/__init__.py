@@ -11,7 +11,7 @@ __version__ = "0.1.0"
 
 
 def __getattr__(name):
-    if name in ("Handle", "build"):
+    if name in ("Handle", "build", "build_batched"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

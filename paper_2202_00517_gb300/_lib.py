@@ -35,7 +35,8 @@ KNND_STOP_MAX_ROUNDS = 3
 EXPORTS = [
     "knnd_create", "knnd_destroy", "knnd_set_stream", "knnd_prepare", "knnd_init_graph", "knnd_round",
     "knnd_fcc", "knnd_sync", "knnd_build", "knnd_build_host", "knnd_get_stats", "knnd_reset_stats",
-    "knnd_status_string", "knnd_version", "knnd_fcc_noalloc",
+    "knnd_status_string", "knnd_version", "knnd_fcc_noalloc", "knnd_batch_create", "knnd_batch_run",
+    "knnd_batch_info", "knnd_batch_destroy", "knnd_build_batched",
 ]
 
 KNND_NOALLOC_MAX_SAMPLES = 1 << 20
@@ -65,6 +66,12 @@ class knnd_stats(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64),
                 ("phase_count", ctypes.c_int64 * KNND_NUM_PHASES),
                 ("phase_ms", ctypes.c_double * KNND_NUM_PHASES)]
+
+
+class knnd_instance(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("ld", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("m", ctypes.c_int32), ("K", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("idx", ctypes.c_void_p), ("key", ctypes.c_void_p)]
 
 
 class KnndError(RuntimeError):
@@ -101,6 +108,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "knnd_status_string": (ctypes.c_char_p, [i32]),
         "knnd_version": (i32, []),
         "knnd_fcc_noalloc": (i32, [P, i64, i32, u64, i32, i32, P, P]),
+        "knnd_batch_create": (i32, [ctypes.POINTER(P), i32, P, i32, i32, ctypes.POINTER(knnd_params), i64, P]),
+        "knnd_batch_run": (i32, [P, P]),
+        "knnd_batch_info": (i32, [P, P, P, P]),
+        "knnd_batch_destroy": (None, [P]),
+        "knnd_build_batched": (i32, [i32, P, i32, i32, ctypes.POINTER(knnd_params), i64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

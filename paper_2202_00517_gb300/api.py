@@ -155,3 +155,40 @@ def build(points, K: int, seed: int = 0, precision: str = "mixed", **kw) -> dict
         return h.build_host(points.contiguous(), seed)
     finally:
         h.close()
+
+
+def build_batched(points_list, Ks, seeds, precision: str = "mixed", fcc_samples: int = 10000,
+                  max_rounds: int = 64, stop_on_zero_updates: bool = True, workspace_limit: int = 0,
+                  stream=None, outputs=None):
+    """Batched form: build many independent instances together.
+
+    points_list: CUDA tensors (n_i x m_i, one dtype for all); Ks, seeds: per instance.
+    Returns a list of dicts (idx, key, rounds, updates, fcc_hits, ...), one per instance.
+    """
+    lib = _lib.load()
+    count = len(points_list)
+    dt = points_list[0].dtype
+    dtype = _DTYPE[dt]
+    arr = (_lib.knnd_instance * count)()
+    outs = []
+    for i, (p, K, sd) in enumerate(zip(points_list, Ks, seeds)):
+        assert p.is_cuda and p.dtype == dt and p.dim() == 2 and p.stride(1) == 1
+        n, m = p.shape
+        if outputs is not None:
+            idx, key = outputs[i]
+        else:
+            idx = torch.empty((n, K), dtype=torch.int32, device=p.device)
+            key = torch.empty((n, K), dtype=torch.float64, device=p.device)
+        outs.append((idx, key))
+        arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, K, sd, idx.data_ptr(), key.data_ptr())
+    prm = _lib.knnd_params(fcc_samples, max_rounds, int(stop_on_zero_updates), 0, 0)
+    infos = (_lib.knnd_build_info * count)()
+    check(lib.knnd_build_batched(count, ctypes.cast(arr, ctypes.c_void_p), dtype, _PREC[precision],
+                                 ctypes.byref(prm), workspace_limit, ctypes.cast(infos, ctypes.c_void_p),
+                                 _stream_ptr(stream)), "knnd_build_batched")
+    res = []
+    for i in range(count):
+        d = _info_dict(infos[i])
+        d.update(idx=outs[i][0], key=outs[i][1])
+        res.append(d)
+    return res

@@ -13,17 +13,6 @@ namespace {
 
 constexpr int32_t kVersion = 100;  // 0.1.0
 
-knnd_params default_params()
-{
-    knnd_params p;
-    p.fcc_samples = 10000;
-    p.max_rounds = KNND_MAX_ROUNDS;
-    p.stop_on_zero_updates = 1;
-    p.debug = 0;
-    p.timing = 0;
-    return p;
-}
-
 knnd_status cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return KNND_OK;
@@ -51,7 +40,8 @@ void free_all(knnd_handle *h)
 {
     void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg,
                     h->cof_off, h->cof, h->scan_tmp, h->tau, h->idxK, h->phi, h->Ex, h->bcnt, h->bkey,
-                    h->bent, h->fb_list, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev};
+                    h->bent, h->fb_list, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev,
+                    h->inst_of, h->inst_base, h->inst_n, h->inst_seed, h->inst_active, h->inst_cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->cnt_host) cudaFreeHost(h->cnt_host);
@@ -155,6 +145,125 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
 
 }  // namespace
 
+namespace knnd {
+
+knnd_params default_params()
+{
+    knnd_params p;
+    p.fcc_samples = 10000;
+    p.max_rounds = KNND_MAX_ROUNDS;
+    p.stop_on_zero_updates = 1;
+    p.debug = 0;
+    p.timing = 0;
+    return p;
+}
+
+void configure(knnd_handle *h, int64_t n, int32_t m, int32_t K)
+{
+    h->n = n;
+    h->m = m;
+    h->MP = pad_coords(m);
+    h->K = K;
+    // c_m of |fp32 dot - fp64 dot| <= c_m sum_i |x_i log y_i|: m FP32 fma roundings,
+    // the FP32 rounding of log y_i and of x_i, doubled-rounding slack; 1% headroom.
+    h->bound_c = (double)(m + 6) * 0x1p-24 * 1.01;
+    h->bucket_cap = n * K * (2 * (int64_t)K + 1);
+    h->prepared = false;
+}
+
+knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd_precision precision,
+                        const knnd_params &prm, void *stream)
+{
+    *out = nullptr;
+    knnd_handle *h = new (std::nothrow) knnd_handle;
+    if (!h) return KNND_ENOMEM;
+    std::memset((void *)h, 0, sizeof(*h));
+    h->dtype = dtype;
+    h->prec = precision;
+    h->prm = prm;
+    h->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return KNND_ECUDA;
+    }
+    const int64_t n = c.n;
+    knnd_status s = KNND_OK;
+    const int64_t ntiles = (n + 2047) / 2048;
+    h->scan_tmp_len = ntiles;
+    const bool mixed = precision != KNND_PREC_FP64;
+    if (!s) s = dalloc(h, &h->X64, c.tab);
+    if (!s) s = dalloc(h, &h->L64, c.tab);
+    if (!s) s = dalloc(h, &h->X32, c.tab);
+    if (!s) s = dalloc(h, &h->L32, c.tab);
+    if (!s) s = dalloc(h, &h->negH, n);
+    if (!s) s = dalloc(h, &h->nx, n);
+    if (!s) s = dalloc(h, &h->smax_bits, c.ninst > 0 ? c.ninst : 1);
+    if (!s) s = dalloc(h, &h->err, 1);
+    if (!s) s = dalloc(h, &h->deg, n);
+    if (!s) s = dalloc(h, &h->cof_off, n + 1);
+    if (!s) s = dalloc(h, &h->cof, c.nK);
+    if (!s) s = dalloc(h, &h->scan_tmp, ntiles);
+    if (!s) s = dalloc(h, &h->tau, n);
+    if (!s) s = dalloc(h, &h->idxK, n);
+    if (!s) s = dalloc(h, &h->phi, n);
+    if (!s) s = dalloc(h, &h->Ex, n);
+    if (!s) s = dalloc(h, &h->bcnt, n);
+    if (!s) s = dalloc(h, &h->bent, c.bucket);
+    if (!s && !mixed) s = dalloc(h, &h->bkey, c.bucket);
+    if (!s) s = dalloc(h, &h->fb_list, n);
+    if (!s) s = dalloc(h, &h->fb_count, 1);
+    if (!s) s = dalloc(h, &h->cnt, kCntNum);
+    if (!s && cudaMallocHost((void **)&h->cnt_host, sizeof(int64_t) * kCntNum) != cudaSuccess) s = KNND_ENOMEM;
+    if (!s && c.ninst > 0) {
+        if (!s) s = dalloc(h, &h->inst_of, n);
+        if (!s) s = dalloc(h, &h->inst_base, c.ninst + 1);
+        if (!s) s = dalloc(h, &h->inst_n, c.ninst);
+        if (!s) s = dalloc(h, &h->inst_seed, c.ninst);
+        if (!s) s = dalloc(h, &h->inst_active, c.ninst);
+        if (!s) s = dalloc(h, &h->inst_cnt, (int64_t)c.ninst * kCntNum);
+    }
+    if (!s && prm.timing) {
+        for (int i = 0; i < 2 * knnd_handle::kMaxPending && !s; ++i)
+            if (cudaEventCreate(&h->ev[i]) != cudaSuccess) s = KNND_ECUDA;
+        h->events_made = true;
+    }
+    if (!s) {
+        cudaError_t e = cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->cnt, 0, sizeof(int64_t) * kCntNum, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        s = cuda_status(e);
+    }
+    if (s) {
+        free_all(h);
+        delete h;
+        (void)cudaGetLastError();
+        return s;
+    }
+    *out = h;
+    return KNND_OK;
+}
+
+void destroy_handle(knnd_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+knnd_status take_error(knnd_handle *h) { return take_device_error(h); }
+
+knnd_status round_ops(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx, double *key, uint8_t *newflag,
+                      int64_t *fcc_hits)
+{
+    return do_round(h, seed, round, idx, key, newflag, fcc_hits);
+}
+
+knnd_status status_of(cudaError_t e) { return cuda_status(e); }
+
+}  // namespace knnd
+
 extern "C" {
 
 const char *knnd_status_string(knnd_status s)
@@ -185,87 +294,25 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     if (dtype != KNND_F32 && dtype != KNND_F64) return KNND_EINVAL;
     if (precision == KNND_PREC_AUTO) precision = KNND_PREC_MIXED_FP32;
     if (precision != KNND_PREC_FP64 && precision != KNND_PREC_MIXED_FP32) return KNND_EINVAL;
-    knnd_params prm = params ? *params : default_params();
+    knnd_params prm = params ? *params : knnd::default_params();
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
     // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
     if ((int64_t)K * K + (int64_t)(K + 1) * (n - 1) >= ((int64_t)1 << 31)) return KNND_EOVERFLOW;
-
-    knnd_handle *h = new (std::nothrow) knnd_handle;
-    if (!h) return KNND_ENOMEM;
-    std::memset((void *)h, 0, sizeof(*h));
-    h->n = n;
-    h->m = m;
-    h->MP = pad_coords(m);
-    h->K = K;
-    h->dtype = dtype;
-    h->prec = precision;
-    h->prm = prm;
-    h->stream = (cudaStream_t)stream;
-    // c_m of |fp32 dot - fp64 dot| <= c_m sum_i |x_i log y_i|: m FP32 fma roundings,
-    // the FP32 rounding of log y_i and of x_i, doubled-rounding slack; 1% headroom.
-    h->bound_c = (double)(m + 6) * 0x1p-24 * 1.01;
-    if (cudaGetDevice(&h->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
-        delete h;
-        return KNND_ECUDA;
-    }
-    const int64_t MP = h->MP, nK = n * K;
-    knnd_status s = KNND_OK;
-    const int64_t ntiles = (n + 2047) / 2048;
-    h->scan_tmp_len = ntiles;
-    const bool mixed = precision != KNND_PREC_FP64;
-    h->bucket_cap = nK * (2 * (int64_t)K + 1);
-    if (!s) s = dalloc(h, &h->X64, n * MP);
-    if (!s) s = dalloc(h, &h->L64, n * MP);
-    if (!s) s = dalloc(h, &h->X32, n * MP);
-    if (!s) s = dalloc(h, &h->L32, n * MP);
-    if (!s) s = dalloc(h, &h->negH, n);
-    if (!s) s = dalloc(h, &h->nx, n);
-    if (!s) s = dalloc(h, &h->smax_bits, 1);
-    if (!s) s = dalloc(h, &h->err, 1);
-    if (!s) s = dalloc(h, &h->deg, n);
-    if (!s) s = dalloc(h, &h->cof_off, n + 1);
-    if (!s) s = dalloc(h, &h->cof, nK);
-    if (!s) s = dalloc(h, &h->scan_tmp, ntiles);
-    if (!s) s = dalloc(h, &h->tau, n);
-    if (!s) s = dalloc(h, &h->idxK, n);
-    if (!s) s = dalloc(h, &h->phi, n);
-    if (!s) s = dalloc(h, &h->Ex, n);
-    if (!s) s = dalloc(h, &h->bcnt, n);
-    if (!s) s = dalloc(h, &h->bent, h->bucket_cap);
-    if (!s && !mixed) s = dalloc(h, &h->bkey, h->bucket_cap);
-    if (!s) s = dalloc(h, &h->fb_list, n);
-    if (!s) s = dalloc(h, &h->fb_count, 1);
-    if (!s) s = dalloc(h, &h->cnt, kCntNum);
-    if (!s && cudaMallocHost((void **)&h->cnt_host, sizeof(int64_t) * kCntNum) != cudaSuccess) s = KNND_ENOMEM;
-    if (!s && prm.timing) {
-        for (int i = 0; i < 2 * knnd_handle::kMaxPending && !s; ++i)
-            if (cudaEventCreate(&h->ev[i]) != cudaSuccess) s = KNND_ECUDA;
-        h->events_made = true;
-    }
-    if (!s) {
-        cudaError_t e = cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->cnt, 0, sizeof(int64_t) * kCntNum, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        s = cuda_status(e);
-    }
-    if (s) {
-        free_all(h);
-        delete h;
-        (void)cudaGetLastError();
-        return s;
-    }
+    knnd::Caps caps;
+    caps.n = n;
+    caps.tab = n * pad_coords(m);
+    caps.nK = n * K;
+    caps.bucket = n * K * (2 * (int64_t)K + 1);
+    caps.ninst = 0;
+    knnd_handle *h = nullptr;
+    knnd_status s = knnd::make_handle(&h, caps, dtype, precision, prm, stream);
+    if (s) return s;
+    knnd::configure(h, n, m, K);
     *out = h;
     return KNND_OK;
 }
 
-void knnd_destroy(knnd_handle *h)
-{
-    if (!h) return;
-    cudaStreamSynchronize(h->stream);
-    free_all(h);
-    delete h;
-}
+void knnd_destroy(knnd_handle *h) { knnd::destroy_handle(h); }
 
 knnd_status knnd_set_stream(knnd_handle *h, void *stream)
 {

@@ -10,7 +10,7 @@ namespace knnd {
 __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *__restrict__ key, int64_t n, int K,
                                  int32_t *__restrict__ deg, double *__restrict__ tau, int32_t *__restrict__ idxK,
                                  const double *__restrict__ negH, const double *__restrict__ nx,
-                                 const unsigned long long *__restrict__ smax_bits, double bound_c,
+                                 const unsigned long long *__restrict__ smax_bits, InstView iv, double bound_c,
                                  float *__restrict__ phi, double *__restrict__ Ex, int32_t *err)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -29,7 +29,7 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
         if (phi) {
             // |fp32 dot - fp64 dot| <= c_m * sum_i |x_i||log y_i| <= c_m * nx(x) * max|log|.
             // margin covers the FP64 roundings of the key and threshold arithmetic.
-            const double smax = __longlong_as_double((long long)*smax_bits);
+            const double smax = __longlong_as_double((long long)smax_bits[iv.at(x)]);
             const double nh = negH[x];
             const double margin = 0x1p-40 * (fabs(nh) + nx[x] * smax + 1.0);
             const double E = bound_c * nx[x] * smax + 0x1p-100 + margin;
@@ -140,7 +140,7 @@ cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double 
     cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
     const bool mixed = h->prec != KNND_PREC_FP64;
     csr_count_kernel<<<eblocks, threads, 0, h->stream>>>(idx, key, n, K, h->deg, h->tau, h->idxK, h->negH, h->nx,
-                                                         h->smax_bits, h->bound_c, mixed ? h->phi : nullptr,
+                                                         h->smax_bits, h->iv, h->bound_c, mixed ? h->phi : nullptr,
                                                          h->Ex, h->err);
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     scan_tiles_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp);

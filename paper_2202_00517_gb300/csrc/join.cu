@@ -47,6 +47,7 @@ struct JoinArgs {
     double *bkey;
     int32_t *err;
     int debug;
+    InstView iv;
 };
 
 __device__ __forceinline__ bool valid_id(int64_t v, int64_t n) { return v >= 0 && v < n; }
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(256, (MP <= 32 ? 3 : 1)) join_mixed_kernel(Joi
     const int cA = 2 * pr, cB = 2 * pr + 1;     // this lane's columns
 
     for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
+        if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
         // column ids of F(v)
         for (int j = lane; j < K; j += 32) {
             int id = a.idx[v * K + j];
@@ -287,6 +289,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
     const unsigned FULL = 0xffffffffu;
 
     for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
+        if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
         int cid[CPL];
         double Lc[CPL][MP];
 #pragma unroll
@@ -489,6 +492,7 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
     a.bkey = h->bkey;
     a.err = h->err;
     a.debug = h->prm.debug;
+    a.iv = h->iv;
     cudaMemsetAsync(h->bcnt, 0, sizeof(int32_t) * h->n, h->stream);
     h->launches += 1;
     switch (h->MP) {

@@ -110,6 +110,20 @@ constexpr int kErrDomain = 1;
 constexpr int kErrBucket = 2;
 constexpr int kErrIndex = 4;
 
+// Instances sharing one handle (the batched form): the union of their
+// graphs, whose arcs never cross instances, is processed as one graph with
+// global point indices.  `of` == nullptr: a single instance covering [0, n).
+struct InstView {
+    const int32_t *of;      // global point -> instance
+    const int64_t *base;    // instance -> its first global point
+    const int32_t *n;       // instance -> its number of points
+    const uint64_t *seed;   // instance -> its seed
+    const int32_t *active;  // instance -> 1 while its rounds continue
+    int64_t *cnt;           // instance -> kCntNum counters of the current round
+    __device__ __forceinline__ int at(int64_t x) const { return of ? of[x] : 0; }
+    __device__ __forceinline__ bool live(int64_t x) const { return !of || active[of[x]] != 0; }
+};
+
 // Device counters of one call (int64 each).
 enum Counter : int {
     kCntUpdates = 0,
@@ -136,7 +150,7 @@ struct knnd_handle {
     // precompute
     double *X64, *L64, *negH, *nx;
     float *X32, *L32;
-    unsigned long long *smax_bits;  // max |log y_i| as the bits of a non-negative double
+    unsigned long long *smax_bits;  // per instance: max |log y_i| as the bits of a non-negative double
     int32_t *err;                   // device error word
     // reverse CSR
     int32_t *deg;     // n: in-degree, then fill cursor
@@ -175,6 +189,15 @@ struct knnd_handle {
     bool events_made;
     double phase_ms[KNND_NUM_PHASES];
     int64_t phase_count[KNND_NUM_PHASES];
+    // batched form: instance tables (device) and their view
+    int32_t ninst;
+    knnd::InstView iv;
+    int32_t *inst_of;
+    int64_t *inst_base;
+    int32_t *inst_n;
+    uint64_t *inst_seed;
+    int32_t *inst_active;
+    int64_t *inst_cnt;
     // statistics
     int64_t launches;
     int64_t rounds_run;
@@ -186,11 +209,32 @@ namespace knnd {
 
 // ---- launch wrappers (each returns cudaGetLastError() of its launches) ----
 cudaError_t launch_precompute(knnd_handle *h, const void *points, int64_t ld);
+cudaError_t launch_precompute_from(knnd_handle *h, const void *points, int64_t ld, const void *const *ptrs,
+                                   const int64_t *lds);
+cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round);
 cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, double *key, uint8_t *newflag);
 cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key);
 cudaError_t launch_join(knnd_handle *h, const int32_t *idx);
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag);
 cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out);
+
+// ---- handle set-up shared by the single-instance and batched forms ----
+struct Caps {
+    int64_t n;       // points
+    int64_t tab;     // elements of each coordinate / log table (points x padded m)
+    int64_t nK;      // arcs
+    int64_t bucket;  // bucket entries
+    int32_t ninst;   // instances (0: single-instance handle)
+};
+knnd_params default_params();
+knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd_precision precision,
+                        const knnd_params &prm, void *stream);
+void configure(knnd_handle *h, int64_t n, int32_t m, int32_t K);
+void destroy_handle(knnd_handle *h);
+knnd_status take_error(knnd_handle *h);
+knnd_status round_ops(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx, double *key, uint8_t *newflag,
+                      int64_t *fcc_hits);
+knnd_status status_of(cudaError_t e);
 
 inline int pad_coords(int m) {
     int mp = (m + 7) / 8 * 8;

@@ -145,7 +145,30 @@ struct MergeArgs {
     int32_t *err;
     int32_t *fb_list;   // rows left to the serial path
     int32_t *fb_count;
+    InstView iv;
 };
+
+// Several instances: a row's counts go to its instance at once.
+__device__ __forceinline__ void flush_row_counts(const MergeArgs &a, int64_t x, int &newcount, long long &rescored,
+                                                 long long &fallbacks)
+{
+    if (!a.iv.of) return;
+    const int nc = __reduce_add_sync(0xffffffffu, newcount);
+    long long rs = rescored, fb = fallbacks;
+    for (int o = 16; o > 0; o >>= 1) {
+        rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        fb += __shfl_xor_sync(0xffffffffu, fb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        int64_t *c = a.iv.cnt + (int64_t)a.iv.of[x] * kCntNum;
+        if (nc) atomicAdd((unsigned long long *)&c[kCntUpdates], (unsigned long long)nc);
+        if (rs) atomicAdd((unsigned long long *)&c[kCntRescored], (unsigned long long)rs);
+        if (fb) atomicAdd((unsigned long long *)&c[kCntFallback], (unsigned long long)fb);
+    }
+    newcount = 0;
+    rescored = 0;
+    fallbacks = 0;
+}
 
 template <int NE>
 __device__ __forceinline__ void write_row(const MergeArgs &a, int64_t x, int lane, const WarpList<NE> &X,
@@ -498,6 +521,7 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
     int newcount = 0;
     long long rescored = 0, fallbacks = 0;
     for (int64_t x = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); x < a.n; x += (int64_t)gridDim.x * wpb) {
+        if (!a.iv.live(x)) continue;  // row of a stopped instance (batched form)
         WarpList<NE> X;
         load_row(a, x, lane, X);
         const int64_t base = (int64_t)K * K * x + (int64_t)(K + 1) * a.cof_off[x];
@@ -511,10 +535,12 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
                 // the row stays as it is here; merge_fallback_kernel finishes it
                 if (lane == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)x;
                 fallbacks += 1;
+                flush_row_counts(a, x, newcount, rescored, fallbacks);
                 continue;
             }
         }
         write_row(a, x, lane, X, newcount);
+        flush_row_counts(a, x, newcount, rescored, fallbacks);
     }
     flush_counts(a, newcount, rescored, fallbacks);
 }
@@ -543,6 +569,8 @@ __global__ void __launch_bounds__(256) merge_fallback_kernel(MergeArgs a)
         hash_fill(tab, lane, K, X);
         serial_row<NE, MIXED>(a, x, lane, X, tab, base, cnt, B, rescored);
         write_row(a, x, lane, X, newcount);
+        long long nofb = 0;
+        flush_row_counts(a, x, newcount, rescored, nofb);
     }
     flush_counts(a, newcount, rescored, 0);
 }
@@ -571,6 +599,7 @@ cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *new
     const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * 8);
     a.fb_list = h->fb_list;
     a.fb_count = h->fb_count;
+    a.iv = h->iv;
     cudaMemsetAsync(h->fb_count, 0, sizeof(int32_t), h->stream);
     const bool fp64 = h->prec == KNND_PREC_FP64;
     const unsigned fgrid = (unsigned)h->num_sms * 2;

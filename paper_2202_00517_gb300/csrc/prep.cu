@@ -14,8 +14,11 @@ namespace knnd {
 // and the largest |L| over all coordinates (the FP32 error-bound scale).
 // Coordinates that are not finite or not > 0 set kErrDomain.
 // ---------------------------------------------------------------------------
+// Points: pts + x * ld, or (several instances) the row x - base[i] of
+// instance i = iv.of[x] at ptrs[i] with row stride lds[i].
 template <typename T>
-__global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, int64_t n, int m, int MP,
+__global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, const void *const *ptrs,
+                                  const int64_t *lds, InstView iv, int64_t n, int m, int MP,
                                   double *__restrict__ X64, double *__restrict__ L64, float *__restrict__ X32,
                                   float *__restrict__ L32, double *__restrict__ negH, double *__restrict__ nx,
                                   unsigned long long *smax_bits, int32_t *err)
@@ -25,7 +28,13 @@ __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, int64_t
     if (x < n) {
         double acc = 0.0, s = 0.0;
         bool bad = false;
-        const T *row = pts + x * ld;
+        const T *row;
+        if (iv.of) {
+            const int i = iv.of[x];
+            row = static_cast<const T *>(ptrs[i]) + (x - iv.base[i]) * lds[i];
+        } else {
+            row = pts + x * ld;
+        }
         for (int i = 0; i < MP; ++i) {
             double v = 0.0, l = 0.0;
             if (i < m) {
@@ -48,6 +57,10 @@ __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, int64_t
         nx[x] = s;
         if (bad) atomicOr(err, kErrDomain);
     }
+    if (iv.of) {  // several instances: one maximum each
+        if (x < n) atomicMax(&smax_bits[iv.of[x]], (unsigned long long)__double_as_longlong(lmax));
+        return;
+    }
     // block max of |L| -> one atomicMax on the (monotone) bits of a non-negative double
     for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
     __shared__ double wmax[32];
@@ -63,17 +76,23 @@ __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, int64_t
 
 cudaError_t launch_precompute(knnd_handle *h, const void *points, int64_t ld)
 {
+    return launch_precompute_from(h, points, ld, nullptr, nullptr);
+}
+
+cudaError_t launch_precompute_from(knnd_handle *h, const void *points, int64_t ld, const void *const *ptrs,
+                                   const int64_t *lds)
+{
     const int threads = 256;
     const int64_t blocks = (h->n + threads - 1) / threads;
-    cudaMemsetAsync(h->smax_bits, 0, sizeof(unsigned long long), h->stream);
+    cudaMemsetAsync(h->smax_bits, 0, sizeof(unsigned long long) * (h->ninst > 0 ? h->ninst : 1), h->stream);
     if (h->dtype == KNND_F32)
         precompute_kernel<float><<<(unsigned)blocks, threads, 0, h->stream>>>(
-            (const float *)points, ld, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32, h->negH, h->nx,
-            h->smax_bits, h->err);
+            (const float *)points, ld, ptrs, lds, h->iv, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32,
+            h->negH, h->nx, h->smax_bits, h->err);
     else
         precompute_kernel<double><<<(unsigned)blocks, threads, 0, h->stream>>>(
-            (const double *)points, ld, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32, h->negH, h->nx,
-            h->smax_bits, h->err);
+            (const double *)points, ld, ptrs, lds, h->iv, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32,
+            h->negH, h->nx, h->smax_bits, h->err);
     h->launches += 1;
     return cudaGetLastError();
 }
@@ -102,17 +121,27 @@ __device__ __forceinline__ double key_fp64(const double *__restrict__ X64, const
 // ---------------------------------------------------------------------------
 __global__ void init_graph_kernel(int64_t n, int K, int MP, const double *__restrict__ X64,
                                   const double *__restrict__ L64, const double *__restrict__ negH, uint64_t seed,
-                                  int32_t *__restrict__ idx, double *__restrict__ key, uint8_t *__restrict__ flag)
+                                  InstView iv, int32_t *__restrict__ idx, double *__restrict__ key,
+                                  uint8_t *__restrict__ flag)
 {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n) return;
+    // several instances: draws use the instance's seed, local indices and size
+    int64_t base = 0, nl = n;
+    if (iv.of) {
+        const int i = iv.of[x];
+        base = iv.base[i];
+        nl = iv.n[i];
+        seed = iv.seed[i];
+    }
+    const int64_t xl = x - base;
     int ids[KNND_MAX_K];
     double ks[KNND_MAX_K];
-    Philox ph(seed, (uint32_t)x, 0u, kTagInit);
+    Philox ph(seed, (uint32_t)xl, 0u, kTagInit);
     int cnt = 0;
     while (cnt < K) {
-        uint32_t yp = ph.bounded((uint32_t)(n - 1));
-        int y = (int)yp + ((int64_t)yp >= x ? 1 : 0);
+        uint32_t yp = ph.bounded((uint32_t)(nl - 1));
+        int y = (int)(base + (int64_t)yp + ((int64_t)yp >= xl ? 1 : 0));
         bool dup = false;
         for (int t = 0; t < cnt; ++t) dup |= (ids[t] == y);
         if (dup) continue;
@@ -143,7 +172,7 @@ cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, doubl
     const int threads = 128;
     const int64_t blocks = (h->n + threads - 1) / threads;
     init_graph_kernel<<<(unsigned)blocks, threads, 0, h->stream>>>(h->n, h->K, h->MP, h->X64, h->L64, h->negH,
-                                                                   seed, idx, key, newflag);
+                                                                   seed, h->iv, idx, key, newflag);
     h->launches += 1;
     return cudaGetLastError();
 }
@@ -189,6 +218,43 @@ __global__ void fcc_kernel(const int32_t *__restrict__ idx, int64_t n, int K, ui
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
         if (t) atomicAdd((unsigned long long *)hits, (unsigned long long)t);
     }
+}
+
+// Several instances: thread (i, s) draws sample s of instance i from its own
+// stream (seed_i, s, round, kTagFcc) over its local indices; hits go to the
+// instance's counter.  Stopped instances draw nothing.
+__global__ void fcc_batch_kernel(const int32_t *__restrict__ idx, int K, InstView iv, int32_t ninst, int32_t round,
+                                 int32_t S, int32_t *err)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)ninst * S) return;
+    const int i = (int)(t / S);
+    const int s = (int)(t - (int64_t)i * S);
+    if (!iv.active[i]) return;
+    const int64_t base = iv.base[i];
+    const int64_t nl = iv.n[i];
+    Philox ph(iv.seed[i], (uint32_t)s, (uint32_t)round, kTagFcc);
+    const int64_t x = base + ph.bounded((uint32_t)nl);
+    const int a = (int)ph.bounded((uint32_t)K);
+    const int bp = (int)ph.bounded((uint32_t)(K - 1));
+    const int b = bp + (bp >= a ? 1 : 0);
+    const int32_t y = idx[x * K + a], z = idx[x * K + b];
+    if (y < base || y >= base + nl || z < base || z >= base + nl) {
+        atomicOr(err, kErrIndex);
+        return;
+    }
+    if (row_has(idx, K, y, z) || row_has(idx, K, z, y))
+        atomicAdd((unsigned long long *)&iv.cnt[(int64_t)i * kCntNum + kCntHits], 1ull);
+}
+
+cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round)
+{
+    const int threads = 256;
+    const int64_t total = (int64_t)h->ninst * h->prm.fcc_samples;
+    fcc_batch_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, h->stream>>>(
+        idx, h->K, h->iv, h->ninst, round, h->prm.fcc_samples, h->err);
+    h->launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out)
