@@ -33,10 +33,16 @@ sys.path.insert(0, ROOT)
 
 from paper_2202_00517_gb300.datagen import dirichlet_points  # noqa: E402
 
-N, M, K, SEED = 1_000_000, 21, 20, 1
 METRIC = "KNN-descent build s & KL evals/s, n=1e6 d=20 K=20: mixed vs FP64, % roofline"
 UNIT = "KL evals/s"
-WORKLOAD = "KL K-NN descent build to the statistical stop, n=1e6 Dirichlet(1) points, d=20 (21 FP32 coords), K=20, seed 1"
+# name -> (n, m, K, seed, description)
+WORKLOADS = {
+    "n1e6_d20_K20": (1_000_000, 21, 20, 1, "KL K-NN descent build to the statistical stop, n=1e6 Dirichlet(1) points, "
+                                            "d=20 (21 FP32 coords), K=20, seed 1"),
+    "n4e6_d64_K32": (4_000_000, 65, 32, 2, "KL K-NN descent build to the statistical stop, n=4e6 Dirichlet(1) points, "
+                                            "d=64 (65 FP32 coords), K=32, seed 2"),
+}
+N, M, K, SEED, WORKLOAD = WORKLOADS["n1e6_d20_K20"]
 REF_ROWS = 100_000  # rows of round 1 the oracle computes per reference step
 
 
@@ -105,11 +111,12 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def join_traffic_per_launch():
-    """DRAM bytes per join launch from the committed ncu summary, if it was taken
-    on the current join source (sha256 recorded in the summary); else None."""
+def join_traffic_per_launch(name):
+    """DRAM bytes per join launch from the committed ncu summary of the workload,
+    if it was taken on the current join source (sha256 recorded in the summary);
+    else None."""
     src = os.path.join(ROOT, "paper_2202_00517_gb300", "csrc", "join.cu")
-    prof = os.path.join(ROOT, "profiles", "join_mixed_n1e6_m21_K20.md")
+    prof = os.path.join(ROOT, "profiles", f"join_mixed_{name}.md")
     if not os.path.exists(prof):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -161,37 +168,15 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------- GPU arm
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    args = ap.parse_args()
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
-
+def gpu_single(args, name, rank, world, local, barrier):
+    """One workload of WORKLOADS: mixed form (the headline), FP64 form beside it, e2e from host memory."""
     import torch
-    import torch.distributed as dist
 
     import paper_2202_00517_gb300 as knnd
 
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
+    N, M, K, SEED, desc = WORKLOADS[name]
     dev = torch.device("cuda", local)
-    pts_host = torch.from_numpy(dirichlet_points(N, M, SEED, np.float32))
+    pts_host = torch.from_numpy(dirichlet_points(N, M, SEED, np.float32, threads=16))
     pts = pts_host.to(dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
@@ -200,14 +185,13 @@ def main():
         h = knnd.Handle(N, M, K, dtype="f32", precision=prec, timing=True)
         idx, key, flag = h.new_graph(dev)
         for _ in range(warmup):
-            out = h.build(pts, SEED, idx, key, flag)
+            h.build(pts, SEED, idx, key, flag)
         h.reset_stats()
         torch.cuda.synchronize()
         barrier()
         if clocks:
             clocks.start()
         ms_total, ev_total, infos = 0.0, 0, []
-        t_wall = time.perf_counter()
         for _ in range(steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -221,15 +205,14 @@ def main():
             infos.append(out)
         torch.cuda.synchronize()
         barrier()
-        wall = time.perf_counter() - t_wall
         clk = clocks.stop() if clocks else None
         st = h.stats()
         h.close()
-        return {"ms": ms_total, "evals": ev_total, "infos": infos, "stats": st, "wall": wall, "clocks": clk}
+        return {"ms": ms_total, "evals": ev_total, "infos": infos, "stats": st, "clocks": clk}
 
     clocks = Clocks(local)
     mixed = run_form("mixed", args.steps, args.warmup, clocks)
-    fp64 = run_form("fp64", args.fp64_steps, 1)
+    fp64 = run_form("fp64", args.fp64_steps, 1) if args.fp64_steps > 0 else None
 
     # end to end through the public API from pinned host memory (H2D points, D2H idx+key)
     h = knnd.Handle(N, M, K, dtype="f32", precision="mixed")
@@ -247,66 +230,214 @@ def main():
         e2e_ev += evals_of(N, K, out["rounds"])
     h.close()
 
-    # max over ranks of the device time
-    t = torch.tensor([mixed["ms"], fp64["ms"], e2e_sec], dtype=torch.float64, device=dev)
+    import torch.distributed as dist
+    t = torch.tensor([mixed["ms"], fp64["ms"] if fp64 else 0.0, e2e_sec], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     mixed_ms, fp64_ms, e2e_max = t.tolist()
+    if rank != 0:
+        return None
+    info = mixed["infos"][-1]
+    st = mixed["stats"]
+    steps = args.steps
+    value = world * mixed["evals"] / (mixed_ms / 1e3)
+    # dominant kernel: the join of the mixed form.  It gathers a random row of
+    # FP32 coordinates or logs per row and column of every hub tile, so HBM
+    # gather traffic bounds it.  Algorithmic bytes per launch: per hub
+    # (K + indeg) rows x (4 MP + 16) + K columns x (4 MP + 4) + (4 MP + 16), summed
+    # over hubs (sum of indeg = nK), plus 8 B per survivor written.
+    join_ms = st["phase_ms"]["join"]
+    join_n = max(1, st["phase_count"]["join"])
+    join_avg_s = join_ms / join_n / 1e3
+    MP = pad_m(M)
+    gather = N * ((2 * K + 1) * (4 * MP + 16) + K * (4 * MP + 4))
+    surv = sum(o["join_survivors"] for o in mixed["infos"]) / max(1, sum(o["rounds"] for o in mixed["infos"]))
+    bytes_per_launch = gather + 8.0 * surv
+    flops_per_launch = 2.0 * M * N * K * (2 * K + 1)
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp32_peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    achieved = bytes_per_launch / join_avg_s / 1e9
+    traffic = join_traffic_per_launch(name)
+    total_ph = max(1e-9, sum(st["phase_ms"].values()))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": mixed_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
+        "config": {"workload": desc, "n": N, "m": M, "K": K, "seed": SEED,
+                   "form": "mixed: FP32 CUDA-core join filter + FP64 re-score (graph == FP64 form)",
+                   "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "build_s_mixed": mixed_ms / steps / 1e3,
+        "rounds": info["rounds"], "updates": info["updates"], "fcc_hits": info["fcc_hits"],
+        "rescored_per_build": info["rescored"], "merge_fallback_rows": info["merge_fallbacks"],
+        "phase_ms_per_build": {p: st["phase_ms"][p] / steps for p in st["phase_ms"]},
+        "phase_share": {p: st["phase_ms"][p] / total_ph for p in st["phase_ms"]},
+        "roofline": {"kernel": f"join_mixed_kernel<{MP}>", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6800 GB/s",
+                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": join_avg_s * 1e3,
+                     "launches_timed": join_n,
+                     "fp32_view": {"flops_per_launch": flops_per_launch,
+                                   "achieved_tflops": flops_per_launch / join_avg_s / 1e12,
+                                   "peak_tflops": fp32_peak,
+                                   "frac": flops_per_launch / join_avg_s / 1e12 / fp32_peak,
+                                   "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"}},
+        "e2e": {"value": world * e2e_ev / e2e_max, "unit": UNIT,
+                "h2d_bytes_per_step": N * M * 4, "d2h_bytes_per_step": N * K * (4 + 8)},
+        "gpu_launches": st["kernel_launches"],
+        "clocks": mixed["clocks"],
+    }
+    if fp64:
+        line["build_s_fp64"] = fp64_ms / max(1, args.fp64_steps) / 1e3
+        line["evals_per_s_fp64"] = world * fp64["evals"] / (fp64_ms / 1e3)
+        line["speedup_mixed_vs_fp64"] = line["build_s_fp64"] / line["build_s_mixed"]
+        line["fp64_join_ms_per_launch"] = fp64["stats"]["phase_ms"]["join"] / max(1, fp64["stats"]["phase_count"]["join"])
+    if not args.no_cpu_baseline and name == "n1e6_d20_K20":
+        import oracle
+        pts64 = pts_host.numpy().astype(np.float64)
+        g0i, _ = oracle.init_graph(pts64, K, SEED)
+        e, s = cpu_reference_step(pts64, g0i)
+        line["cpu_baseline"] = {
+            "value": e / s, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"oracle round 1 for rows [0, {REF_ROWS}) of the n=1e6 workload from its own initial "
+                       f"graph ({e} evaluations in {s:.2f} s, setup over all n included)")}
+    return line
 
-    if rank == 0:
-        info = mixed["infos"][-1]
-        st = mixed["stats"]
-        steps = args.steps
-        value = world * mixed["evals"] / (mixed_ms / 1e3)
-        # dominant kernel: the join (mixed form), FP32 FMA pipe bound
-        join_ms = st["phase_ms"]["join"]
-        join_n = max(1, st["phase_count"]["join"])
-        join_avg_s = join_ms / join_n / 1e3
-        flops_per_launch = 2.0 * M * N * K * (2 * K + 1)
-        peaks, peak_kind = measured_peaks()
-        clk = mixed["clocks"] or {}
-        sm_mhz = 2070.0
-        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
-        achieved = flops_per_launch / join_avg_s / 1e12
-        traffic = join_traffic_per_launch()
-        phase_share = {p: (st["phase_ms"][p] / max(1e-9, sum(st["phase_ms"].values()))) for p in st["phase_ms"]}
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": mixed_ms / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N, "m": M, "K": K, "seed": SEED,
-                       "form": "mixed: FP32 CUDA-core join filter + FP64 re-score (graph == FP64 form)",
-                       "l2": "flushed between steps (256 MiB write, outside the step events)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "build_s_mixed": mixed_ms / steps / 1e3,
-            "build_s_fp64": fp64_ms / max(1, args.fp64_steps) / 1e3,
-            "evals_per_s_fp64": world * fp64["evals"] / (fp64_ms / 1e3),
-            "speedup_mixed_vs_fp64": (fp64_ms / max(1, args.fp64_steps)) / (mixed_ms / steps),
-            "rounds": info["rounds"], "updates": info["updates"], "fcc_hits": info["fcc_hits"],
-            "rescored_per_build": info["rescored"], "merge_fallback_rows": info["merge_fallbacks"],
-            "phase_ms_per_build": {p: st["phase_ms"][p] / steps for p in st["phase_ms"]},
-            "phase_share": phase_share,
-            "roofline": {"kernel": "join_mixed_kernel<24,1>", "bound": "alu", "achieved": achieved,
-                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                         "traffic": traffic,
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)",
-                         "flops_per_launch": flops_per_launch, "avg_launch_ms": join_avg_s * 1e3,
-                         "launches_timed": join_n,
-                         "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind},
-            "e2e": {"value": world * e2e_ev / e2e_max, "unit": UNIT,
-                    "h2d_bytes_per_step": N * M * 4, "d2h_bytes_per_step": N * K * (4 + 8)},
-            "gpu_launches": st["kernel_launches"],
-            "clocks": clk,
-        }
-        if not args.no_cpu_baseline:
-            import oracle
-            pts64 = pts_host.numpy().astype(np.float64)
-            g0i, _ = oracle.init_graph(pts64, K, SEED)
-            e, s = cpu_reference_step(pts64, g0i)
-            line["cpu_baseline"] = {
-                "value": e / s, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                "sample": (f"oracle round 1 for rows [0, {REF_ROWS}) of the n=1e6 workload from its own initial "
-                           f"graph ({e} evaluations in {s:.2f} s, setup over all n included)")}
+
+def gpu_batch(args, rank, world, local, barrier):
+    """The 4096-instance mix: batched form vs separate builds (a sample, scaled)."""
+    import ctypes
+
+    import torch
+
+    import paper_2202_00517_gb300 as knnd
+    from paper_2202_00517_gb300 import _lib
+    from paper_2202_00517_gb300.datagen import instance_mix
+
+    count, per_inst = 4096, args.batch_sample
+    mix = instance_mix(count, 5)
+    dev = torch.device("cuda", local)
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(16) as ex:
+        host = list(ex.map(lambda a: dirichlet_points(a[1][0], a[1][1], 0x5EED0000 + a[0], np.float32),
+                           enumerate(mix)))
+    pts = [torch.from_numpy(hh).to(dev) for hh in host]
+    Ks = [k for _, _, k in mix]
+    seeds = [0x5EED0000 + i for i in range(count)]
+    lib = _lib.load()
+    arr = (_lib.knnd_instance * count)()
+    outs = []
+    for i, (p, k) in enumerate(zip(pts, Ks)):
+        n, m = p.shape
+        idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+        key = torch.empty((n, k), dtype=torch.float64, device=dev)
+        outs.append((idx, key))
+        arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, k, seeds[i], idx.data_ptr(), key.data_ptr())
+    prm = _lib.knnd_params(10000, 64, 1, 0, 0)
+    b = ctypes.c_void_p()
+    st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    _lib.check(lib.knnd_batch_create(ctypes.byref(b), count, ctypes.cast(arr, ctypes.c_void_p), _lib.KNND_F32,
+                                     _lib.KNND_PREC_MIXED_FP32, ctypes.byref(prm), 0, st), "knnd_batch_create")
+    infos = (_lib.knnd_build_info * count)()
+    for _ in range(args.warmup):
+        _lib.check(lib.knnd_batch_run(b, ctypes.cast(infos, ctypes.c_void_p)), "knnd_batch_run")
+    l0 = ctypes.c_int64()
+    lib.knnd_batch_info(b, None, None, ctypes.byref(l0))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _lib.check(lib.knnd_batch_run(b, ctypes.cast(infos, ctypes.c_void_p)), "knnd_batch_run")
+    torch.cuda.synchronize()
+    batched_s = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    nsub, ws, l1 = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    lib.knnd_batch_info(b, ctypes.byref(nsub), ctypes.byref(ws), ctypes.byref(l1))
+    lib.knnd_batch_destroy(b)
+    evals = sum(evals_of(n, k, infos[i].rounds) for i, (n, m, k) in enumerate(mix))
+    # separate builds on an evenly spaced sample, bit-identity checked, time scaled to all instances
+    sel = np.linspace(0, count - 1, per_inst).astype(int)
+    sep, same = 0.0, 0
+    for i in sel:
+        n, m = pts[i].shape
+        h = knnd.Handle(n, m, Ks[i], dtype="f32", precision="mixed")
+        h.build(pts[i], seeds[i])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = h.build(pts[i], seeds[i])
+        torch.cuda.synchronize()
+        sep += time.perf_counter() - t1
+        same += int(torch.equal(r["idx"], outs[i][0]) and torch.equal(r["key"], outs[i][1])
+                    and r["rounds"] == infos[i].rounds)
+        h.close()
+    sep_est = sep / len(sel) * count
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": world * evals / batched_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": batched_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
+        "config": {"workload": "batched form: 4096 independent instances, n log-uniform in [200, 50000], "
+                               "d in {5, 10, 20}, K in {8, 16, 32}, Dirichlet(1), seeds 0x5EED0000+i",
+                   "points": int(sum(n for n, _, _ in mix)), "sub_batches": nsub.value,
+                   "workspace_gb": ws.value / 1e9, "l2": "inputs larger than L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "batched_s": batched_s, "separate_builds_s_est": sep_est,
+        "separate_sample": f"{len(sel)} evenly spaced instances, each timed on its own warm handle, scaled to 4096",
+        "speedup_batched_vs_separate": sep_est / batched_s,
+        "identical_instances": f"{same}/{len(sel)}",
+        "rounds_mean": float(np.mean([infos[i].rounds for i in range(count)])),
+        "gpu_launches": (l1.value - l0.value) // max(1, args.steps),
+        "clocks": clk,
+    }
+
+
+def pad_m(m):
+    mp = (m + 7) // 8 * 8
+    for lo, hi, v in ((32, 48, 48), (48, 64, 64), (64, 72, 72), (72, 96, 96), (96, 128, 128)):
+        if lo < mp <= hi:
+            return v
+    return mp
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="n1e6_d20_K20", choices=list(WORKLOADS) + ["batch4096"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--batch-sample", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    if args.workload == "batch4096":
+        line = gpu_batch(args, rank, world, local, barrier)
+    else:
+        line = gpu_single(args, args.workload, rank, world, local, barrier)
+    if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     barrier()
     if world > 1:

@@ -96,6 +96,7 @@ typedef struct {
     int64_t rescored;                        /* mixed forms: pairs re-scored in FP64 */
     int64_t bound_violations;                /* debug audit: FP32 errors above the bound (must be 0) */
     int64_t merge_fallbacks;                 /* rows the merge finished on its serial path */
+    int64_t join_survivors;                  /* candidates the join passed to the merge, all rounds */
 } knnd_build_info;
 
 /* Phases of the descent, for the per-phase timing of knnd_stats. */

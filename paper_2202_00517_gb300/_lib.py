@@ -54,7 +54,7 @@ class knnd_build_info(ctypes.Structure):
                 ("fcc_hits", ctypes.c_int64 * (KNND_MAX_ROUNDS + 1)),
                 ("proposals", ctypes.c_int64), ("init_pairs", ctypes.c_int64),
                 ("rescored", ctypes.c_int64), ("bound_violations", ctypes.c_int64),
-                ("merge_fallbacks", ctypes.c_int64)]
+                ("merge_fallbacks", ctypes.c_int64), ("join_survivors", ctypes.c_int64)]
 
 
 KNND_NUM_PHASES = 6

@@ -37,7 +37,7 @@ def _info_dict(info: _lib.knnd_build_info) -> dict:
             "fcc_hits": [info.fcc_hits[i] for i in range(r + 1)],
             "proposals": info.proposals, "init_pairs": info.init_pairs,
             "rescored": info.rescored, "bound_violations": info.bound_violations,
-            "merge_fallbacks": info.merge_fallbacks}
+            "merge_fallbacks": info.merge_fallbacks, "join_survivors": info.join_survivors}
 
 
 class Handle:

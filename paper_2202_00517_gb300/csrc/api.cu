@@ -416,6 +416,7 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
         info->rescored += hst[kCntRescored];
         info->bound_violations += hst[kCntBoundViol];
         info->merge_fallbacks += hst[kCntFallback];
+        info->join_survivors += hst[kCntSurvivors];
         info->proposals += per_round;
         info->rounds = r;
         if (info->fcc_hits[r] <= info->fcc_hits[r - 1]) {

@@ -131,6 +131,7 @@ enum Counter : int {
     kCntRescored = 2,
     kCntBoundViol = 3,
     kCntFallback = 4,
+    kCntSurvivors = 5,  // bucket entries the join wrote
     kCntNum = 8
 };
 

@@ -216,8 +216,10 @@ __device__ __forceinline__ int bucket_count(const MergeArgs &a, int64_t x)
 }
 
 __device__ __forceinline__ void flush_counts(const MergeArgs &a, int newcount, long long rescored,
-                                             long long fallbacks)
+                                             long long fallbacks, long long survivors = 0)
 {
+    if ((threadIdx.x & 31) == 0 && survivors)
+        atomicAdd((unsigned long long *)&a.cnt[kCntSurvivors], (unsigned long long)survivors);
     newcount = __reduce_add_sync(0xffffffffu, newcount);
     for (int o = 16; o > 0; o >>= 1) {
         rescored += __shfl_xor_sync(0xffffffffu, rescored, o);
@@ -519,13 +521,14 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
     int *tab = s_hash[threadIdx.x >> 5];
     int2 *live_list = s_live[threadIdx.x >> 5];
     int newcount = 0;
-    long long rescored = 0, fallbacks = 0;
+    long long rescored = 0, fallbacks = 0, survivors = 0;
     for (int64_t x = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); x < a.n; x += (int64_t)gridDim.x * wpb) {
         if (!a.iv.live(x)) continue;  // row of a stopped instance (batched form)
         WarpList<NE> X;
         load_row(a, x, lane, X);
         const int64_t base = (int64_t)K * K * x + (int64_t)(K + 1) * a.cof_off[x];
         const int cnt = bucket_count(a, x);
+        survivors += cnt;
         if (cnt > 0) {
             Bounds<MIXED> B;
             B.nh = MIXED ? a.negH[x] : 0.0;
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
         write_row(a, x, lane, X, newcount);
         flush_row_counts(a, x, newcount, rescored, fallbacks);
     }
-    flush_counts(a, newcount, rescored, fallbacks);
+    flush_counts(a, newcount, rescored, fallbacks, survivors);
 }
 
 // Rows the fast path could not settle, one warp each, on the serial path.

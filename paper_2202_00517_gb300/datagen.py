@@ -44,23 +44,39 @@ def _philox_blocks(c0: np.ndarray, c1: int, c2: int, c3: int, seed: int) -> np.n
     return np.stack([x0, x1, x2, x3], axis=1).astype(np.uint32)
 
 
-def dirichlet_points(n: int, m: int, seed: int, dtype=np.float32, chunk: int = 1 << 18) -> np.ndarray:
-    """n points uniform on the (m-1)-simplex (m coordinates), shape (n, m)."""
+def _rows(start: int, stop: int, m: int, seed: int) -> np.ndarray:
+    """Points start..stop-1 of the stream, float64, shape (stop - start, m)."""
+    nblocks = (2 * m + 3) // 4
+    c0 = np.arange(start, stop, dtype=np.uint64)
+    words = np.concatenate([_philox_blocks(c0, 0, 2, j, seed) for j in range(nblocks)], axis=1)
+    hi = words[:, 0:2 * m:2].astype(np.uint64)
+    lo = words[:, 1:2 * m:2].astype(np.uint64)
+    k = ((hi << np.uint64(32)) | lo) >> np.uint64(11)
+    u = (k.astype(np.float64) + 0.5) * (2.0 ** -53)
+    e = -np.log(u)
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def dirichlet_points(n: int, m: int, seed: int, dtype=np.float32, chunk: int = 1 << 18,
+                     threads: int = 1) -> np.ndarray:
+    """n points uniform on the (m-1)-simplex (m coordinates), shape (n, m).
+    The values do not depend on `chunk` or `threads` (host threads over row chunks)."""
     if n < 0 or m < 1:
         raise ValueError("need n >= 0, m >= 1")
     out = np.empty((n, m), dtype=dtype)
-    nblocks = (2 * m + 3) // 4
-    for start in range(0, n, chunk):
+
+    def part(start):
         stop = min(n, start + chunk)
-        c0 = np.arange(start, stop, dtype=np.uint64)
-        words = np.concatenate([_philox_blocks(c0, 0, 2, j, seed) for j in range(nblocks)], axis=1)
-        hi = words[:, 0:2 * m:2].astype(np.uint64)
-        lo = words[:, 1:2 * m:2].astype(np.uint64)
-        k = ((hi << np.uint64(32)) | lo) >> np.uint64(11)
-        u = (k.astype(np.float64) + 0.5) * (2.0 ** -53)
-        e = -np.log(u)
-        x = e / e.sum(axis=1, keepdims=True)
-        out[start:stop] = x.astype(dtype)
+        out[start:stop] = _rows(start, stop, m, seed).astype(dtype)
+
+    starts = range(0, n, chunk)
+    if threads > 1:
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(threads) as ex:
+            list(ex.map(part, starts))
+    else:
+        for st in starts:
+            part(st)
     return out
 
 

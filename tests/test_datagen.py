@@ -37,3 +37,9 @@ def test_instance_mix():
     u = np.log(ns / 200) / np.log(250)
     assert stats.kstest(u, "uniform").pvalue > 1e-3
     assert mix == instance_mix(4096, 5)
+
+
+def test_threads_and_chunks_do_not_change_values():
+    a = dirichlet_points(3000, 7, 9, np.float32)
+    b = dirichlet_points(3000, 7, 9, np.float32, chunk=256, threads=4)
+    assert np.array_equal(a, b)
