@@ -39,7 +39,7 @@ knnd_status dalloc(knnd_handle *h, T **p, int64_t count)
 void free_all(knnd_handle *h)
 {
     void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg,
-                    h->cof_off, h->cof, h->scan_tmp, h->tau, h->idxK, h->phi, h->Ex, h->bcnt, h->bkey,
+                    h->cof_off, h->cof, h->scan_tmp, h->tau, h->idxK, h->meta, h->Ex, h->bcnt, h->bkey,
                     h->bent, h->fb_list, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev,
                     h->inst_of, h->inst_base, h->inst_n, h->inst_seed, h->inst_active, h->inst_cnt};
     for (void *p : ptrs)
@@ -206,7 +206,7 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
     if (!s) s = dalloc(h, &h->scan_tmp, ntiles);
     if (!s) s = dalloc(h, &h->tau, n);
     if (!s) s = dalloc(h, &h->idxK, n);
-    if (!s) s = dalloc(h, &h->phi, n);
+    if (!s) s = dalloc(h, &h->meta, n);
     if (!s) s = dalloc(h, &h->Ex, n);
     if (!s) s = dalloc(h, &h->bcnt, n);
     if (!s) s = dalloc(h, &h->bent, c.bucket);

@@ -11,7 +11,7 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
                                  int32_t *__restrict__ deg, double *__restrict__ tau, int32_t *__restrict__ idxK,
                                  const double *__restrict__ negH, const double *__restrict__ nx,
                                  const unsigned long long *__restrict__ smax_bits, InstView iv, double bound_c,
-                                 float *__restrict__ phi, double *__restrict__ Ex, int32_t *err)
+                                 RowMeta *__restrict__ meta, double *__restrict__ Ex, int32_t *err)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * K) return;
@@ -26,7 +26,7 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
         const double t = key[e];
         tau[x] = t;
         idxK[x] = v;
-        if (phi) {
+        if (meta) {
             // |fp32 dot - fp64 dot| <= c_m * sum_i |x_i||log y_i| <= c_m * nx(x) * max|log|.
             // margin covers the FP64 roundings of the key and threshold arithmetic.
             const double smax = __longlong_as_double((long long)smax_bits[iv.at(x)]);
@@ -34,7 +34,7 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
             const double margin = 0x1p-40 * (fabs(nh) + nx[x] * smax + 1.0);
             const double E = bound_c * nx[x] * smax + 0x1p-100 + margin;
             Ex[x] = E;
-            phi[x] = __double2float_rd(nh - t - E);
+            meta[x].phi = __double2float_rd(nh - t - E);
         }
     }
 }
@@ -100,7 +100,7 @@ __global__ void scan_sums_kernel(int64_t *__restrict__ tile_sum, int64_t ntiles,
 }
 
 __global__ void scan_apply_kernel(const int32_t *__restrict__ deg, int64_t n, const int64_t *__restrict__ tile_off,
-                                  int64_t *__restrict__ off)
+                                  int64_t *__restrict__ off, RowMeta *__restrict__ meta, int K)
 {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
     int64_t v[kScanPer];
@@ -112,7 +112,10 @@ __global__ void scan_apply_kernel(const int32_t *__restrict__ deg, int64_t n, co
     __shared__ int64_t tot;
     int64_t run = block_exclusive_scan(s, &tot) + tile_off[blockIdx.x];
     for (int i = 0; i < kScanPer; ++i) {
-        if (base + i < n) off[base + i] = run;
+        if (base + i < n) {
+            off[base + i] = run;
+            if (meta) meta[base + i].boff = (long long)K * K * (base + i) + (long long)(K + 1) * run;
+        }
         run += v[i];
     }
 }
@@ -140,12 +143,13 @@ cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double 
     cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
     const bool mixed = h->prec != KNND_PREC_FP64;
     csr_count_kernel<<<eblocks, threads, 0, h->stream>>>(idx, key, n, K, h->deg, h->tau, h->idxK, h->negH, h->nx,
-                                                         h->smax_bits, h->iv, h->bound_c, mixed ? h->phi : nullptr,
+                                                         h->smax_bits, h->iv, h->bound_c, mixed ? h->meta : nullptr,
                                                          h->Ex, h->err);
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     scan_tiles_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp);
     scan_sums_kernel<<<1, kScanThreads, 0, h->stream>>>(h->scan_tmp, ntiles, h->cof_off, n);
-    scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp, h->cof_off);
+    scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp, h->cof_off,
+                                                                        mixed ? h->meta : nullptr, K);
     cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
     csr_fill_kernel<<<eblocks, threads, 0, h->stream>>>(idx, n, K, h->cof_off, h->deg, h->cof);
     h->launches += 5;

@@ -41,7 +41,7 @@ struct JoinArgs {
     const double *negH;
     const double *tau;
     const int32_t *idxK;
-    const float *phi;
+    const RowMeta *meta;
     int32_t *bcnt;
     int2 *bent;
     double *bkey;
@@ -147,8 +147,9 @@ __global__ void __launch_bounds__(256, (MP <= 32 ? 3 : 1)) join_mixed_kernel(Joi
             int64_t roff = 0;
             float4 *srow = reinterpret_cast<float4 *>(sX + lane * S::RS);
             if (rid >= 0) {
-                ph = a.phi[rid];
-                roff = (int64_t)K * K * rid + (int64_t)(K + 1) * a.cof_off[rid];
+                const RowMeta rm = a.meta[rid];
+                ph = rm.phi;
+                roff = rm.boff;
                 const float4 *xr = reinterpret_cast<const float4 *>(a.X32 + (int64_t)rid * MP);
 #pragma unroll
                 for (int i4 = 0; i4 < MP / 4; ++i4) srow[i4] = __ldg(xr + i4);
@@ -486,7 +487,7 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
     a.negH = h->negH;
     a.tau = h->tau;
     a.idxK = h->idxK;
-    a.phi = h->phi;
+    a.meta = h->meta;
     a.bcnt = h->bcnt;
     a.bent = h->bent;
     a.bkey = h->bkey;

@@ -124,6 +124,15 @@ struct InstView {
     __device__ __forceinline__ bool live(int64_t x) const { return !of || active[of[x]] != 0; }
 };
 
+// Per-row data the mixed join reads with every row it gathers, packed in one
+// 16-byte record (one memory sector): the rejection threshold phi and the
+// start of the row's bucket, K*K*x + (K+1)*cof_off[x].
+struct __align__(16) RowMeta {
+    float phi;
+    int32_t pad;
+    long long boff;
+};
+
 // Device counters of one call (int64 each).
 enum Counter : int {
     kCntUpdates = 0,
@@ -162,7 +171,7 @@ struct knnd_handle {
     // per-row thresholds of the join filter
     double *tau;  // n: K-th key of the row
     int32_t *idxK;  // n: K-th index of the row
-    float *phi;   // n: mixed form, dot-space rejection threshold
+    knnd::RowMeta *meta;  // n: mixed form, rejection threshold and bucket start of each row
     double *Ex;   // n: mixed form, error bound of the FP32 dot
     // buckets
     int32_t *bcnt;  // n
