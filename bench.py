@@ -211,11 +211,11 @@ def gpu_single(args, name, rank, world, local, barrier):
         return {"ms": ms_total, "evals": ev_total, "infos": infos, "stats": st, "clocks": clk}
 
     clocks = Clocks(local)
-    mixed = run_form("mixed", args.steps, args.warmup, clocks)
+    mixed = run_form(args.form, args.steps, args.warmup, clocks)
     fp64 = run_form("fp64", args.fp64_steps, 1) if args.fp64_steps > 0 else None
 
     # end to end through the public API from pinned host memory (H2D points, D2H idx+key)
-    h = knnd.Handle(N, M, K, dtype="f32", precision="mixed")
+    h = knnd.Handle(N, M, K, dtype="f32", precision=args.form)
     ph = pts_host.pin_memory()
     idx_h = torch.empty((N, K), dtype=torch.int32, pin_memory=True)
     key_h = torch.empty((N, K), dtype=torch.float64, pin_memory=True)
@@ -265,7 +265,9 @@ def gpu_single(args, name, rank, world, local, barrier):
         "warmup": args.warmup, "ms_per_step": mixed_ms / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
         "config": {"workload": desc, "n": N, "m": M, "K": K, "seed": SEED,
-                   "form": "mixed: FP32 CUDA-core join filter + FP64 re-score (graph == FP64 form)",
+                   "form": ("mixed: FP32 CUDA-core join filter + FP64 re-score (graph == FP64 form)"
+                            if args.form == "mixed" else
+                            "mixed: BF16 hi/lo x3 tcgen05 join tiles, FP32 accumulate + FP64 re-score (graph == FP64 form)"),
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "build_s_mixed": mixed_ms / steps / 1e3,
@@ -273,7 +275,8 @@ def gpu_single(args, name, rank, world, local, barrier):
         "rescored_per_build": info["rescored"], "merge_fallback_rows": info["merge_fallbacks"],
         "phase_ms_per_build": {p: st["phase_ms"][p] / steps for p in st["phase_ms"]},
         "phase_share": {p: st["phase_ms"][p] / total_ph for p in st["phase_ms"]},
-        "roofline": {"kernel": f"join_mixed_kernel<{MP}>", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": f"join_mixed_kernel<{MP}>" if args.form == "mixed" else f"join_tc_kernel<{MP}>",
+                     "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6800 GB/s",
@@ -412,6 +415,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="n1e6_d20_K20", choices=list(WORKLOADS) + ["batch4096"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--form", default="mixed", choices=["mixed", "bf16x3"],
+                    help="headline mixed form: FP32 CUDA-core join or BF16x3 tcgen05 join")
     ap.add_argument("--batch-sample", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -65,6 +65,7 @@ typedef int32_t knnd_dtype;
 typedef int32_t knnd_precision;
 #define KNND_PREC_FP64 0        /* every pair scored in FP64 */
 #define KNND_PREC_MIXED_FP32 1  /* FP32 CUDA-core filter + FP64 re-score */
+#define KNND_PREC_MIXED_BF16X3 2 /* BF16 hi/lo split tiles on the tcgen05 tensor cores + FP64 re-score */
 #define KNND_PREC_AUTO 3        /* the library chooses (currently MIXED_FP32) */
 
 #define KNND_MAX_K 64
@@ -94,9 +95,10 @@ typedef struct {
     int64_t proposals;                       /* candidate pairs scored by the join, all rounds */
     int64_t init_pairs;                      /* pairs scored by the initial graph (n*K) */
     int64_t rescored;                        /* mixed forms: pairs re-scored in FP64 */
-    int64_t bound_violations;                /* debug audit: FP32 errors above the bound (must be 0) */
+    int64_t bound_violations;                /* debug audit: low-precision errors above the bound (must be 0) */
     int64_t merge_fallbacks;                 /* rows the merge finished on its serial path */
     int64_t join_survivors;                  /* candidates the join passed to the merge, all rounds */
+    int64_t bound_audited;                   /* debug audit: pairs whose low-precision dot was checked */
 } knnd_build_info;
 
 /* Phases of the descent, for the per-phase timing of knnd_stats. */

@@ -22,6 +22,7 @@ KNND_F32 = 0
 KNND_F64 = 1
 KNND_PREC_FP64 = 0
 KNND_PREC_MIXED_FP32 = 1
+KNND_PREC_MIXED_BF16X3 = 2
 KNND_PREC_AUTO = 3
 
 KNND_MAX_K = 64
@@ -54,7 +55,8 @@ class knnd_build_info(ctypes.Structure):
                 ("fcc_hits", ctypes.c_int64 * (KNND_MAX_ROUNDS + 1)),
                 ("proposals", ctypes.c_int64), ("init_pairs", ctypes.c_int64),
                 ("rescored", ctypes.c_int64), ("bound_violations", ctypes.c_int64),
-                ("merge_fallbacks", ctypes.c_int64), ("join_survivors", ctypes.c_int64)]
+                ("merge_fallbacks", ctypes.c_int64), ("join_survivors", ctypes.c_int64),
+                ("bound_audited", ctypes.c_int64)]
 
 
 KNND_NUM_PHASES = 6

@@ -15,7 +15,8 @@ from . import _lib
 from ._lib import check
 
 _PREC = {"fp64": _lib.KNND_PREC_FP64, "mixed": _lib.KNND_PREC_MIXED_FP32,
-         "mixed_fp32": _lib.KNND_PREC_MIXED_FP32, "auto": _lib.KNND_PREC_AUTO}
+         "mixed_fp32": _lib.KNND_PREC_MIXED_FP32, "bf16x3": _lib.KNND_PREC_MIXED_BF16X3,
+         "auto": _lib.KNND_PREC_AUTO}
 _DTYPE = {"f32": _lib.KNND_F32, "f64": _lib.KNND_F64, torch.float32: _lib.KNND_F32,
           torch.float64: _lib.KNND_F64}
 
@@ -37,7 +38,8 @@ def _info_dict(info: _lib.knnd_build_info) -> dict:
             "fcc_hits": [info.fcc_hits[i] for i in range(r + 1)],
             "proposals": info.proposals, "init_pairs": info.init_pairs,
             "rescored": info.rescored, "bound_violations": info.bound_violations,
-            "merge_fallbacks": info.merge_fallbacks, "join_survivors": info.join_survivors}
+            "merge_fallbacks": info.merge_fallbacks, "join_survivors": info.join_survivors,
+            "bound_audited": info.bound_audited}
 
 
 class Handle:

@@ -62,6 +62,7 @@ knnd_status take_device_error(knnd_handle *h)
     cudaStreamSynchronize(h->stream);
     if (e & kErrDomain) return KNND_EDOMAIN;
     if (e & kErrIndex) return KNND_EINVAL;
+    if (e & kErrTimeout) return KNND_ETIMEOUT;
     return KNND_EOVERFLOW;
 }
 
@@ -167,6 +168,7 @@ void configure(knnd_handle *h, int64_t n, int32_t m, int32_t K)
     // c_m of |fp32 dot - fp64 dot| <= c_m sum_i |x_i log y_i|: m FP32 fma roundings,
     // the FP32 rounding of log y_i and of x_i, doubled-rounding slack; 1% headroom.
     h->bound_c = (double)(m + 6) * 0x1p-24 * 1.01;
+    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, K)) h->bound_c = bound_c_bf16x3(h->MP);
     h->bucket_cap = n * K * (2 * (int64_t)K + 1);
     h->prepared = false;
 }
@@ -293,7 +295,8 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     if (K < 2 || K > KNND_MAX_K || (int64_t)K >= n) return KNND_EINVAL;
     if (dtype != KNND_F32 && dtype != KNND_F64) return KNND_EINVAL;
     if (precision == KNND_PREC_AUTO) precision = KNND_PREC_MIXED_FP32;
-    if (precision != KNND_PREC_FP64 && precision != KNND_PREC_MIXED_FP32) return KNND_EINVAL;
+    if (precision != KNND_PREC_FP64 && precision != KNND_PREC_MIXED_FP32 && precision != KNND_PREC_MIXED_BF16X3)
+        return KNND_EINVAL;
     knnd_params prm = params ? *params : knnd::default_params();
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
     // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
@@ -417,6 +420,7 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
         info->bound_violations += hst[kCntBoundViol];
         info->merge_fallbacks += hst[kCntFallback];
         info->join_survivors += hst[kCntSurvivors];
+        info->bound_audited += hst[kCntAudited];
         info->proposals += per_round;
         info->rounds = r;
         if (info->fcc_hits[r] <= info->fcc_hits[r - 1]) {

@@ -306,7 +306,8 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
     if (count < 1 || !inst) return KNND_EINVAL;
     if (dtype != KNND_F32 && dtype != KNND_F64) return KNND_EINVAL;
     if (precision == KNND_PREC_AUTO) precision = KNND_PREC_MIXED_FP32;
-    if (precision != KNND_PREC_FP64 && precision != KNND_PREC_MIXED_FP32) return KNND_EINVAL;
+    if (precision != KNND_PREC_FP64 && precision != KNND_PREC_MIXED_FP32 && precision != KNND_PREC_MIXED_BF16X3)
+        return KNND_EINVAL;
     knnd_params prm = params ? *params : default_params();
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
     if (prm.timing) prm.timing = 0;  // phase timing is a single-instance feature

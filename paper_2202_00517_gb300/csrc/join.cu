@@ -474,6 +474,7 @@ static cudaError_t run_join_cpl(knnd_handle *h, const JoinArgs &a)
 
 cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
 {
+    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K)) return launch_join_tc(h, idx);
     JoinArgs a;
     a.n = h->n;
     a.K = h->K;

@@ -109,6 +109,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 constexpr int kErrDomain = 1;
 constexpr int kErrBucket = 2;
 constexpr int kErrIndex = 4;
+constexpr int kErrTimeout = 8;
 
 // Instances sharing one handle (the batched form): the union of their
 // graphs, whose arcs never cross instances, is processed as one graph with
@@ -141,6 +142,7 @@ enum Counter : int {
     kCntBoundViol = 3,
     kCntFallback = 4,
     kCntSurvivors = 5,  // bucket entries the join wrote
+    kCntAudited = 6,    // pairs checked by the bound audit (debug)
     kCntNum = 8
 };
 
@@ -225,6 +227,9 @@ cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round);
 cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, double *key, uint8_t *newflag);
 cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key);
 cudaError_t launch_join(knnd_handle *h, const int32_t *idx);
+cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx);
+double bound_c_bf16x3(int MP);
+bool tc_supported(int MP, int K);
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag);
 cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out);
 

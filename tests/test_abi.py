@@ -42,10 +42,10 @@ def test_version_and_status_strings(lib):
 
 
 def test_struct_layouts():
-    # host structs of the header: five int32 params; build info 8 + 64*8 + 65*8 + 6*8 bytes;
+    # host structs of the header: five int32 params; build info 8 + 64*8 + 65*8 + 7*8 bytes;
     # stats 3 int64 + 6 int64 + 6 double
     assert ctypes.sizeof(_lib.knnd_params) == 20
-    assert ctypes.sizeof(_lib.knnd_build_info) == 8 + 64 * 8 + 65 * 8 + 6 * 8
+    assert ctypes.sizeof(_lib.knnd_build_info) == 8 + 64 * 8 + 65 * 8 + 7 * 8
     assert ctypes.sizeof(_lib.knnd_stats) == 3 * 8 + 6 * 8 + 6 * 8
 
 

@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ("fp64", "mixed")
+PRECS = ("fp64", "mixed", "bf16x3")
 
 
 @pytest.fixture(scope="module")
@@ -132,19 +132,41 @@ def test_duplicated_points_exact_ties(knnd, prec):
     assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
 
 
-def test_mixed_equals_fp64_bitwise(knnd):
-    n, m, K, seed = 200_000, 21, 20, 1
+@pytest.mark.parametrize("n,m,K", [(200_000, 21, 20), (60_000, 65, 32)])
+def test_mixed_forms_equal_fp64_bitwise(knnd, n, m, K):
+    seed = 1
     pts = _dev(dirichlet_points(n, m, seed, np.float32))
     res = {}
     for prec in PRECS:
         h = knnd.Handle(n, m, K, dtype="f32", precision=prec)
         res[prec] = h.build(pts, seed)
         h.close()
-    a, b = res["fp64"], res["mixed"]
-    assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"]
-    assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["key"], b["key"])
-    assert b["rescored"] > 0
-    check_invariants(b["idx"].cpu().numpy(), b["key"].cpu().numpy())
+    a = res["fp64"]
+    for prec in ("mixed", "bf16x3"):
+        b = res[prec]
+        assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"], prec
+        assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["key"], b["key"]), prec
+        assert b["rescored"] > 0
+    check_invariants(a["idx"].cpu().numpy(), a["key"].cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["mixed", "bf16x3"])
+@pytest.mark.parametrize("m,K", [(21, 20), (65, 32), (6, 10)])
+def test_error_bound_audit(knnd, prec, m, K):
+    # debug mode checks every low-precision dot the tensor-core join computes
+    # against the FP64 dot: none may exceed the bound the filter relies on
+    n = 6000
+    pts = _dev(dirichlet_points(n, m, 17, np.float32))
+    h = knnd.Handle(n, m, K, dtype="f32", precision=prec, debug=True)
+    out = h.build(pts, 17)
+    h.close()
+    assert out["bound_violations"] == 0
+    if prec == "bf16x3":
+        assert out["bound_audited"] > n * K
+    ref = knnd.Handle(n, m, K, dtype="f32", precision="fp64")
+    r = ref.build(pts, 17)
+    ref.close()
+    assert torch.equal(out["idx"], r["idx"]) and torch.equal(out["key"], r["key"])
 
 
 def test_domain_errors_and_recovery(knnd):
