@@ -75,8 +75,14 @@ struct MixedSmem {
     static __host__ __device__ int warp_bytes(int K) { return off_rb(K) + 8 * 32; }
 };
 
+// Resident blocks of 128 threads per SM the kernel is compiled for: the
+// register budget grows with the two MP-wide column registers of each lane
+// (spill-free at every MP; measured best at n = 4e5..1e6: 20 warps per SM for
+// MP <= 16, 16 for MP 24..32).
+__host__ __device__ constexpr int mixed_min_blocks(int MP) { return MP <= 16 ? 5 : (MP <= 32 ? 4 : 2); }
+
 template <int MP>
-__global__ void __launch_bounds__(256, (MP <= 32 ? 3 : 1)) join_mixed_kernel(JoinArgs a)
+__global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(JoinArgs a)
 {
     using S = MixedSmem<MP>;
     extern __shared__ float4 smem4[];
@@ -98,26 +104,97 @@ __global__ void __launch_bounds__(256, (MP <= 32 ? 3 : 1)) join_mixed_kernel(Joi
     const bool active = g < G;
     const int cA = 2 * pr, cB = 2 * pr + 1;     // this lane's columns
 
-    for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
-        if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
-        // column ids of F(v)
-        for (int j = lane; j < K; j += 32) {
-            int id = a.idx[v * K + j];
-            if (!valid_id(id, n)) {
-                atomicOr(a.err, kErrIndex);
-                id = -1;
-            }
-            sCid[j] = id;
+    // Short rows and K <= 32: the hub's ids come in one step (the columns F(v) are
+    // also its first K rows), then its column log rows and its first chunk of
+    // rows in a second, all in flight together; the columns are staged in the dot
+    // buffer (stride CS) until each lane has read its two.  cof_off is read one
+    // hub ahead.
+    const bool fast = MP <= 32 && K <= 32;
+    const int CS = (K * (MP + 4) <= 32 * DS) ? MP + 4 : MP;
+    const int64_t vstep = (int64_t)gridDim.x * wpb;
+    int64_t v = (int64_t)blockIdx.x * wpb + warp;
+    int64_t nc0 = 0, nc1 = 0;
+    if (v < n) {
+        nc0 = a.cof_off[v];
+        nc1 = a.cof_off[v + 1];
+    }
+    for (; v < n; v += vstep) {
+        const int64_t c0 = nc0, c1 = nc1;
+        if (v + vstep < n) {
+            nc0 = a.cof_off[v + vstep];
+            nc1 = a.cof_off[v + vstep + 1];
         }
+        if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
+        const int64_t nrows = (int64_t)K + (c1 - c0);
         // the hub's own log row: column v of the co-friend pairs, row slot 32
         for (int i4 = lane; i4 < MP / 4; i4 += 32)
             reinterpret_cast<float4 *>(sX + 32 * S::RS)[i4] =
                 __ldg(reinterpret_cast<const float4 *>(a.L32 + v * MP) + i4);
+        int rid0 = -1;  // fast: this lane's row of the first chunk
+        if (fast) {
+            if (lane < nrows) {
+                rid0 = lane < K ? a.idx[v * K + lane] : a.cof[c0 + (lane - K)];
+                if (!valid_id(rid0, n)) {
+                    atomicOr(a.err, kErrIndex);
+                    rid0 = -1;
+                }
+            }
+            if (lane < K) sCid[lane] = rid0;
+        } else {
+            for (int j = lane; j < K; j += 32) {
+                int id = a.idx[v * K + j];
+                if (!valid_id(id, n)) {
+                    atomicOr(a.err, kErrIndex);
+                    id = -1;
+                }
+                sCid[j] = id;
+            }
+        }
         __syncwarp();
         const int idA = (active && cA < K) ? sCid[cA] : -1;
         const int idB = (active && cB < K) ? sCid[cB] : -1;
         float LA[MP], LB[MP];
-        {
+        float ph0 = 0.f;
+        int64_t roff0 = 0;
+        if (fast) {
+            constexpr int Q = MP / 4;
+            float4 cv[Q], xv[Q];
+#pragma unroll
+            for (int t = 0; t < Q; ++t) {
+                const int i = lane + 32 * t, j = i / Q, c = i - j * Q;
+                const int id = j < K ? sCid[j] : -1;
+                cv[t] = id >= 0 ? __ldg(reinterpret_cast<const float4 *>(a.L32 + (int64_t)id * MP) + c)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const float4 *xr = reinterpret_cast<const float4 *>(a.X32 + (int64_t)(rid0 < 0 ? 0 : rid0) * MP);
+#pragma unroll
+            for (int i4 = 0; i4 < Q; ++i4) xv[i4] = rid0 >= 0 ? __ldg(xr + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rid0 >= 0) {
+                const RowMeta rm = a.meta[rid0];
+                ph0 = rm.phi;
+                roff0 = rm.boff;
+            }
+            float4 *sC4 = reinterpret_cast<float4 *>(sD);
+#pragma unroll
+            for (int t = 0; t < Q; ++t) {
+                const int i = lane + 32 * t, j = i / Q, c = i - j * Q;
+                if (j < K) sC4[j * (CS / 4) + c] = cv[t];
+            }
+            float4 *srow = reinterpret_cast<float4 *>(sX + lane * S::RS);
+#pragma unroll
+            for (int i4 = 0; i4 < Q; ++i4) srow[i4] = xv[i4];
+            __syncwarp();
+            const float4 *ra = sC4 + (idA >= 0 ? cA : 0) * (CS / 4);
+            const float4 *rb = sC4 + (idB >= 0 ? cB : 0) * (CS / 4);
+#pragma unroll
+            for (int i4 = 0; i4 < Q; ++i4) {
+                const float4 ta = idA >= 0 ? ra[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 tb = idB >= 0 ? rb[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                LA[4 * i4 + 0] = ta.x; LA[4 * i4 + 1] = ta.y; LA[4 * i4 + 2] = ta.z; LA[4 * i4 + 3] = ta.w;
+                LB[4 * i4 + 0] = tb.x; LB[4 * i4 + 1] = tb.y; LB[4 * i4 + 2] = tb.z; LB[4 * i4 + 3] = tb.w;
+            }
+            __syncwarp();  // the dot buffer is written by the scoring below
+        } else {
             const float4 *ra = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(idA < 0 ? 0 : idA) * MP);
             const float4 *rb = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(idB < 0 ? 0 : idB) * MP);
 #pragma unroll
@@ -129,35 +206,39 @@ __global__ void __launch_bounds__(256, (MP <= 32 ? 3 : 1)) join_mixed_kernel(Joi
             }
         }
 
-        const int64_t c0 = a.cof_off[v];
-        const int64_t nrows = (int64_t)K + (a.cof_off[v + 1] - c0);
         for (int64_t base = 0; base < nrows; base += 32) {
             const int nr = (int)min((int64_t)32, nrows - base);
             // stage: lane t <-> row t of the chunk
             const int64_t r = base + lane;
             int rid = -1;
-            if (r < nrows) {
-                rid = (r < K) ? a.idx[v * K + r] : a.cof[c0 + (r - K)];
-                if (!valid_id(rid, n)) {
-                    atomicOr(a.err, kErrIndex);
-                    rid = -1;
-                }
-            }
             float ph = 0.f;
             int64_t roff = 0;
-            float4 *srow = reinterpret_cast<float4 *>(sX + lane * S::RS);
-            if (rid >= 0) {
-                const RowMeta rm = a.meta[rid];
-                ph = rm.phi;
-                roff = rm.boff;
-                const float4 *xr = reinterpret_cast<const float4 *>(a.X32 + (int64_t)rid * MP);
-#pragma unroll
-                for (int i4 = 0; i4 < MP / 4; ++i4) srow[i4] = __ldg(xr + i4);
+            if (fast && base == 0) {  // staged above
+                rid = rid0;
+                ph = ph0;
+                roff = roff0;
             } else {
+                if (r < nrows) {
+                    rid = (r < K) ? a.idx[v * K + r] : a.cof[c0 + (r - K)];
+                    if (!valid_id(rid, n)) {
+                        atomicOr(a.err, kErrIndex);
+                        rid = -1;
+                    }
+                }
+                float4 *srow = reinterpret_cast<float4 *>(sX + lane * S::RS);
+                if (rid >= 0) {
+                    const RowMeta rm = a.meta[rid];
+                    ph = rm.phi;
+                    roff = rm.boff;
+                    const float4 *xr = reinterpret_cast<const float4 *>(a.X32 + (int64_t)rid * MP);
 #pragma unroll
-                for (int i4 = 0; i4 < MP / 4; ++i4) srow[i4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int i4 = 0; i4 < MP / 4; ++i4) srow[i4] = __ldg(xr + i4);
+                } else {
+#pragma unroll
+                    for (int i4 = 0; i4 < MP / 4; ++i4) srow[i4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                __syncwarp();
             }
-            __syncwarp();
             // score: group g takes rows it*2G + 2g and +1
             for (int r0 = 2 * g; r0 < nr; r0 += 2 * G) {
                 if (!active) break;
@@ -452,7 +533,7 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         join_fp64_kernel<MP, CPL><<<(unsigned)grid, threads, smem, h->stream>>>(a);
     } else {
         using S = MixedSmem<MP>;
-        const int threads = 256;
+        const int threads = 128;
         const size_t smem = (size_t)S::warp_bytes(h->K) * (threads / 32);
         cudaFuncSetAttribute(join_mixed_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
