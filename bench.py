@@ -185,8 +185,8 @@ def gpu_single(args, name, rank, world, local, barrier):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
-    def run_form(prec, steps, warmup, clocks=None):
-        h = knnd.Handle(N, M, K, dtype="f32", precision=prec, timing=True)
+    def run_form(prec, steps, warmup, clocks=None, incremental=False):
+        h = knnd.Handle(N, M, K, dtype="f32", precision=prec, timing=True, incremental=incremental)
         idx, key, flag = h.new_graph(dev)
         for _ in range(warmup):
             h.build(pts, SEED, idx, key, flag)
@@ -217,6 +217,8 @@ def gpu_single(args, name, rank, world, local, barrier):
     clocks = Clocks(local)
     mixed = run_form(args.form, args.steps, args.warmup, clocks)
     fp64 = run_form("fp64", args.fp64_steps, 1) if args.fp64_steps > 0 else None
+    # the same build with incremental proposals (same graph, fewer candidates), one step
+    incr = run_form(args.form, 1, 1, incremental=True) if args.steps > 0 else None
 
     # end to end through the public API from pinned host memory (H2D points, D2H idx+key)
     h = knnd.Handle(N, M, K, dtype="f32", precision=args.form)
@@ -272,11 +274,13 @@ def gpu_single(args, name, rank, world, local, barrier):
                    "form": ("mixed: FP32 CUDA-core join filter + FP64 re-score (graph == FP64 form)"
                             if args.form == "mixed" else
                             "mixed: BF16 hi/lo x3 tcgen05 join tiles, FP32 accumulate + FP64 re-score (graph == FP64 form)"),
+                   "proposals": "every pair the hub tiles meet (the paper's full pool)",
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "build_s_mixed": mixed_ms / steps / 1e3,
         "rounds": info["rounds"], "updates": info["updates"], "fcc_hits": info["fcc_hits"],
         "rescored_per_build": info["rescored"], "merge_fallback_rows": info["merge_fallbacks"],
+        "join_survivors_per_build": info["join_survivors"],
         "phase_ms_per_build": {p: st["phase_ms"][p] / steps for p in st["phase_ms"]},
         "phase_share": {p: st["phase_ms"][p] / total_ph for p in st["phase_ms"]},
         "roofline": {"kernel": f"join_mixed_kernel<{MP}>" if args.form == "mixed" else f"join_tc_kernel<{MP}>",
@@ -296,6 +300,15 @@ def gpu_single(args, name, rank, world, local, barrier):
         "gpu_launches": st["kernel_launches"],
         "clocks": mixed["clocks"],
     }
+    if incr:
+        a_info = incr["infos"][-1]
+        line["incremental_proposals"] = {
+            "build_s": incr["ms"] / 1e3, "join_survivors_per_build": a_info["join_survivors"],
+            "join_ms_per_launch": incr["stats"]["phase_ms"]["join"] / max(1, incr["stats"]["phase_count"]["join"]),
+            "merge_ms_per_launch": incr["stats"]["phase_ms"]["merge"] / max(1, incr["stats"]["phase_count"]["merge"])}
+        line["incremental_proposals"]["same_graph"] = bool(
+            a_info["rounds"] == info["rounds"] and a_info["updates"] == info["updates"]
+            and torch.equal(a_info["idx"], info["idx"]) and torch.equal(a_info["key"], info["key"]))
     if fp64:
         line["build_s_fp64"] = fp64_ms / max(1, args.fp64_steps) / 1e3
         line["evals_per_s_fp64"] = world * fp64["evals"] / (fp64_ms / 1e3)
@@ -342,7 +355,7 @@ def gpu_batch(args, rank, world, local, barrier):
         key = torch.empty((n, k), dtype=torch.float64, device=dev)
         outs.append((idx, key))
         arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, k, seeds[i], idx.data_ptr(), key.data_ptr())
-    prm = _lib.knnd_params(10000, 64, 1, 0, 0)
+    prm = _lib.knnd_params(10000, 64, 1, 0, 0, 0)
     b = ctypes.c_void_p()
     st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     _lib.check(lib.knnd_batch_create(ctypes.byref(b), count, ctypes.cast(arr, ctypes.c_void_p), _lib.KNND_F32,

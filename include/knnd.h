@@ -79,6 +79,8 @@ typedef struct {
     int32_t stop_on_zero_updates; /* also stop after a round with no update (1) */
     int32_t debug;                /* 1: device bounds checks and error-bound audit (0) */
     int32_t timing;               /* 1: CUDA events around every phase, see knnd_stats (0) */
+    int32_t incremental;          /* 1: a round does not propose again a pair it met only through edges
+                                     of the previous round's graph (0); see knnd_round */
 } knnd_params;
 
 /* Why knnd_build stopped. */
@@ -158,6 +160,13 @@ knnd_status knnd_init_graph(knnd_handle *h, const void *points, int64_t ld, uint
  * rows sorted by (key, idx)); newflag (device n x K or NULL) marks the
  * entries of G_r absent from G_{r-1}.  Pool of x: friends, co-friends,
  * friends of friends, friends of co-friends, minus x; G_r(x) = its K best.
+ * Incremental proposals (params.incremental = 1 and newflag non-NULL):
+ * newflag is also read on entry, as the flags of G_{r-1} that the previous
+ * knnd_init_graph / knnd_round call wrote for this graph (all 1 for a graph
+ * from elsewhere).  A pair the hub tiles meet only through edges whose flag
+ * is 0 was in round r-1's pool already, so it is either in G_{r-1}(x) or
+ * worse than its K-th entry, and is not proposed again: the result is the
+ * same graph with fewer candidates to merge.  Every pair is still scored.
  * updates (device int64 or NULL) receives the number of new entries;
  * fcc_hits (device int64 or NULL) receives the clustering hits of G_r drawn
  * from stream (seed, counter (s, r, 1, block)) for s < fcc_samples

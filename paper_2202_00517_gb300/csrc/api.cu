@@ -39,7 +39,7 @@ knnd_status dalloc(knnd_handle *h, T **p, int64_t count)
 void free_all(knnd_handle *h)
 {
     void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg,
-                    h->cof_off, h->cof, h->scan_tmp, h->tau, h->idxK, h->meta, h->Ex, h->bcnt, h->bkey,
+                    h->cof_off, h->cof, h->cof_new, h->flag_tmp, h->scan_tmp, h->tau, h->idxK, h->meta, h->Ex, h->bcnt, h->bkey,
                     h->bent, h->fb_list, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev,
                     h->inst_of, h->inst_base, h->inst_n, h->inst_seed, h->inst_active, h->inst_cnt};
     for (void *p : ptrs)
@@ -122,6 +122,9 @@ knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
 knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx, double *key, uint8_t *newflag,
                      int64_t *fcc_hits)
 {
+    // incremental proposals read the flags of G_{r-1} (the join runs before the
+    // merge overwrites them with those of G_r)
+    h->round_flag = (h->prm.incremental && newflag) ? newflag : nullptr;
     int t = phase_begin(h);
     cudaError_t e = launch_reverse_csr(h, idx, key);
     phase_end(h, t, KNND_PHASE_CSR);
@@ -140,6 +143,7 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
         e = launch_fcc(h, idx, seed, round, fcc_hits);
         phase_end(h, t, KNND_PHASE_FCC);
     }
+    h->round_flag = nullptr;
     h->rounds_run += 1;
     return cuda_status(e);
 }
@@ -156,6 +160,7 @@ knnd_params default_params()
     p.stop_on_zero_updates = 1;
     p.debug = 0;
     p.timing = 0;
+    p.incremental = 0;
     return p;
 }
 
@@ -205,6 +210,8 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
     if (!s) s = dalloc(h, &h->deg, n);
     if (!s) s = dalloc(h, &h->cof_off, n + 1);
     if (!s) s = dalloc(h, &h->cof, c.nK);
+    if (!s && prm.incremental) s = dalloc(h, &h->cof_new, c.nK);
+    if (!s && prm.incremental) s = dalloc(h, &h->flag_tmp, c.nK);
     if (!s) s = dalloc(h, &h->scan_tmp, ntiles);
     if (!s) s = dalloc(h, &h->tau, n);
     if (!s) s = dalloc(h, &h->idxK, n);
@@ -299,6 +306,7 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
         return KNND_EINVAL;
     knnd_params prm = params ? *params : knnd::default_params();
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
+    if (prm.incremental != 0 && prm.incremental != 1) return KNND_EINVAL;
     // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
     if ((int64_t)K * K + (int64_t)(K + 1) * (n - 1) >= ((int64_t)1 << 31)) return KNND_EOVERFLOW;
     knnd::Caps caps;
@@ -386,6 +394,7 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
     std::memset(info, 0, sizeof(*info));
     knnd_status s = do_prepare(h, points, ld);
     if (s) return s;
+    if (!newflag && h->prm.incremental) newflag = h->flag_tmp;  // the rounds need the flags
     int t = phase_begin(h);
     cudaError_t e = launch_init_graph(h, seed, idx, key, newflag);
     phase_end(h, t, KNND_PHASE_INIT);

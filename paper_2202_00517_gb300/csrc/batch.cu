@@ -180,11 +180,11 @@ void batch_free(knnd_batch *b)
 }
 
 // Device bytes one point of an instance with (m, K) needs in the workspace.
-int64_t bytes_per_point(int32_t m, int32_t K, bool mixed)
+int64_t bytes_per_point(int32_t m, int32_t K, bool mixed, bool incremental)
 {
     const int64_t MP = pad_coords(m);
     const int64_t bucket = (int64_t)K * (2 * K + 1) * (mixed ? 8 : 16);
-    return MP * 24 + 96 + bucket + (int64_t)K * (4 + 4 + 8);
+    return MP * 24 + 96 + bucket + (int64_t)K * (4 + 4 + 8 + (incremental ? 2 : 0));
 }
 
 // One sub-batch: all its instances from points to graphs.
@@ -240,7 +240,8 @@ knnd_status run_sub(knnd_batch *b, const SubBatch &sb, knnd_build_info *info)
     if (e) return status_of(e);
     knnd_status s = take_error(h);
     if (s) return s;
-    e = launch_init_graph(h, 0, b->idx, b->key, nullptr);
+    uint8_t *flag = b->prm.incremental ? h->flag_tmp : nullptr;  // incremental proposals
+    e = launch_init_graph(h, 0, b->idx, b->key, flag);
     if (!e) e = cudaMemsetAsync(h->inst_cnt, 0, sizeof(int64_t) * ni * kCntNum, st);
     if (!e) e = launch_fcc_batch(h, b->idx, 0);
     if (e) return status_of(e);
@@ -250,7 +251,7 @@ knnd_status run_sub(knnd_batch *b, const SubBatch &sb, knnd_build_info *info)
         e = cudaMemsetAsync(h->inst_cnt, 0, sizeof(int64_t) * ni * kCntNum, st);
         if (!e) e = cudaMemsetAsync(b->hs.nactive, 0, sizeof(int32_t), st);
         if (e) return status_of(e);
-        s = round_ops(h, 0, r, b->idx, b->key, nullptr, nullptr);
+        s = round_ops(h, 0, r, b->idx, b->key, flag, nullptr);
         if (s) return s;
         e = launch_fcc_batch(h, b->idx, r);
         if (e) return status_of(e);
@@ -310,6 +311,7 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
         return KNND_EINVAL;
     knnd_params prm = params ? *params : default_params();
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
+    if (prm.incremental != 0 && prm.incremental != 1) return KNND_EINVAL;
     if (prm.timing) prm.timing = 0;  // phase timing is a single-instance feature
     const bool mixed = precision != KNND_PREC_FP64;
     for (int32_t i = 0; i < count; ++i) {
@@ -333,7 +335,7 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
     Caps caps = {0, 0, 0, 0, 0};
     for (auto &kv : classes) {
         const int32_t m = kv.first.first, K = kv.first.second;
-        const int64_t bpp = bytes_per_point(m, K, mixed);
+        const int64_t bpp = bytes_per_point(m, K, mixed, prm.incremental != 0);
         SubBatch cur{m, K, {}, 0};
         auto flush = [&]() {
             if (cur.members.empty()) return;

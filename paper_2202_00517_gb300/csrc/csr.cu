@@ -122,8 +122,10 @@ __global__ void scan_apply_kernel(const int32_t *__restrict__ deg, int64_t n, co
 
 // One thread per arc x -> v: append x to coF(v).  The order inside a list is
 // not fixed; every consumer treats the list as a set.
+// With flag (incremental proposals), the arc's new-flag goes with it.
 __global__ void csr_fill_kernel(const int32_t *__restrict__ idx, int64_t n, int K, const int64_t *__restrict__ off,
-                                int32_t *__restrict__ cursor, int32_t *__restrict__ cof)
+                                int32_t *__restrict__ cursor, int32_t *__restrict__ cof,
+                                const uint8_t *__restrict__ flag, uint8_t *__restrict__ cof_new)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * K) return;
@@ -131,6 +133,7 @@ __global__ void csr_fill_kernel(const int32_t *__restrict__ idx, int64_t n, int 
     if (v < 0 || v >= n) return;
     const int32_t p = atomicAdd(&cursor[v], 1);
     cof[off[v] + p] = (int32_t)(e / K);
+    if (flag) cof_new[off[v] + p] = flag[e];
 }
 
 cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key)
@@ -151,7 +154,8 @@ cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double 
     scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp, h->cof_off,
                                                                         mixed ? h->meta : nullptr, K);
     cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
-    csr_fill_kernel<<<eblocks, threads, 0, h->stream>>>(idx, n, K, h->cof_off, h->deg, h->cof);
+    csr_fill_kernel<<<eblocks, threads, 0, h->stream>>>(idx, n, K, h->cof_off, h->deg, h->cof, h->round_flag,
+                                                        h->cof_new);
     h->launches += 5;
     return cudaGetLastError();
 }

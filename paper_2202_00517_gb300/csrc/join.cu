@@ -48,7 +48,20 @@ struct JoinArgs {
     int32_t *err;
     int debug;
     InstView iv;
+    // incremental proposals: flags of G_{r-1} (n x K) and of the coF entries,
+    // or NULL (every pair proposed).  A pair met only through arcs whose flag
+    // is 0 was in the previous round's pool and is not proposed again.
+    const uint8_t *flag;
+    const uint8_t *cof_new;
 };
+
+// New-flag of the arc that makes row r (of hub v) a row of the tile: v -> x
+// for the first K rows (x in F(v)), x -> v for the co-friend rows.
+__device__ __forceinline__ int row_new(const JoinArgs &a, int64_t v, int K, int64_t c0, int64_t r)
+{
+    if (!a.flag) return 1;
+    return r < K ? a.flag[v * K + r] : a.cof_new[c0 + (r - K)];
+}
 
 __device__ __forceinline__ bool valid_id(int64_t v, int64_t n) { return v >= 0 && v < n; }
 
@@ -72,16 +85,22 @@ struct MixedSmem {
     static __host__ __device__ int off_j(int K) { return off_cid(K) + 4 * 64; }
     static __host__ __device__ int off_inc(int K) { return off_j(K) + ((32 * K + 15) & ~15); }
     static __host__ __device__ int off_rb(int K) { return off_inc(K) + 4 * 32; }
-    static __host__ __device__ int warp_bytes(int K) { return off_rb(K) + 8 * 32; }
+    static __host__ __device__ int off_cnew(int K) { return off_rb(K) + 8 * 32; }
+    static __host__ __device__ int warp_bytes(int K) { return off_cnew(K) + 64; }
 };
 
 // Resident blocks of 128 threads per SM the kernel is compiled for: the
 // register budget grows with the two MP-wide column registers of each lane
 // (spill-free at every MP; measured best at n = 4e5..1e6: 20 warps per SM for
-// MP <= 16, 16 for MP 24..32).
-__host__ __device__ constexpr int mixed_min_blocks(int MP) { return MP <= 16 ? 5 : (MP <= 32 ? 4 : 2); }
+// MP <= 16, 16 for MP 24..32, 8 for MP 48..96; MP = 128 scores in 32-wide
+// coordinate chunks and fits 12).
+__host__ __device__ constexpr int mixed_min_blocks(int MP) {
+    return MP <= 16 ? 5 : (MP <= 32 ? 4 : (MP <= 96 ? 2 : 3));
+}
 
-template <int MP>
+// INC: incremental proposals (a.flag non-NULL); compiled apart so that the
+// default form carries none of its state.
+template <int MP, bool INC>
 __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(JoinArgs a)
 {
     using S = MixedSmem<MP>;
@@ -97,6 +116,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
     unsigned char *sJ = wbase + S::off_j(K);
     int *sInc = reinterpret_cast<int *>(wbase + S::off_inc(K));
     int64_t *sRB = reinterpret_cast<int64_t *>(wbase + S::off_rb(K));
+    unsigned char *sCnew = wbase + S::off_cnew(K);  // new-flags of the columns
     const int64_t n = a.n;
     const int npairs = (K + 1) >> 1;
     const int G = 32 / npairs;                 // row groups
@@ -131,15 +151,20 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
             reinterpret_cast<float4 *>(sX + 32 * S::RS)[i4] =
                 __ldg(reinterpret_cast<const float4 *>(a.L32 + v * MP) + i4);
         int rid0 = -1;  // fast: this lane's row of the first chunk
+        int rnew0 = 1;
         if (fast) {
             if (lane < nrows) {
                 rid0 = lane < K ? a.idx[v * K + lane] : a.cof[c0 + (lane - K)];
+                if (INC) rnew0 = row_new(a, v, K, c0, lane);
                 if (!valid_id(rid0, n)) {
                     atomicOr(a.err, kErrIndex);
                     rid0 = -1;
                 }
             }
-            if (lane < K) sCid[lane] = rid0;
+            if (lane < K) {
+                sCid[lane] = rid0;
+                if (INC) sCnew[lane] = (unsigned char)rnew0;
+            }
         } else {
             for (int j = lane; j < K; j += 32) {
                 int id = a.idx[v * K + j];
@@ -148,12 +173,22 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                     id = -1;
                 }
                 sCid[j] = id;
+                if (INC) sCnew[j] = (unsigned char)row_new(a, v, K, c0, j);
             }
         }
         __syncwarp();
+        // no new column: only rows reached through a new arc can propose
+        const bool any_col_new =
+            !INC || __any_sync(0xffffffffu, lane < K && sCnew[lane]) ||
+            (K > 32 && __any_sync(0xffffffffu, lane + 32 < K && sCnew[lane + 32]));
         const int idA = (active && cA < K) ? sCid[cA] : -1;
         const int idB = (active && cB < K) ? sCid[cB] : -1;
-        float LA[MP], LB[MP];
+        // MP = 128: two columns' log rows do not fit in registers; the scoring runs
+        // over CHK coordinates at a time, the partial dots carried in the dot buffer
+        // (the same fma chain, in the same order)
+        constexpr int CHK = MP <= 96 ? MP : 32;
+        constexpr int NCH = MP / CHK;
+        float LA[CHK], LB[CHK];
         float ph0 = 0.f;
         int64_t roff0 = 0;
         if (fast) {
@@ -194,11 +229,11 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 LB[4 * i4 + 0] = tb.x; LB[4 * i4 + 1] = tb.y; LB[4 * i4 + 2] = tb.z; LB[4 * i4 + 3] = tb.w;
             }
             __syncwarp();  // the dot buffer is written by the scoring below
-        } else {
+        } else if (NCH == 1) {
             const float4 *ra = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(idA < 0 ? 0 : idA) * MP);
             const float4 *rb = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(idB < 0 ? 0 : idB) * MP);
 #pragma unroll
-            for (int i4 = 0; i4 < MP / 4; ++i4) {
+            for (int i4 = 0; i4 < CHK / 4; ++i4) {
                 const float4 ta = (idA >= 0) ? __ldg(ra + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float4 tb = (idB >= 0) ? __ldg(rb + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
                 LA[4 * i4 + 0] = ta.x; LA[4 * i4 + 1] = ta.y; LA[4 * i4 + 2] = ta.z; LA[4 * i4 + 3] = ta.w;
@@ -211,15 +246,18 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
             // stage: lane t <-> row t of the chunk
             const int64_t r = base + lane;
             int rid = -1;
+            int rnew = 1;
             float ph = 0.f;
             int64_t roff = 0;
             if (fast && base == 0) {  // staged above
                 rid = rid0;
+                rnew = rnew0;
                 ph = ph0;
                 roff = roff0;
             } else {
                 if (r < nrows) {
                     rid = (r < K) ? a.idx[v * K + r] : a.cof[c0 + (r - K)];
+                    if (INC) rnew = row_new(a, v, K, c0, r);
                     if (!valid_id(rid, n)) {
                         atomicOr(a.err, kErrIndex);
                         rid = -1;
@@ -240,44 +278,69 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 __syncwarp();
             }
             // score: group g takes rows it*2G + 2g and +1
-            for (int r0 = 2 * g; r0 < nr; r0 += 2 * G) {
-                if (!active) break;
-                const int r1 = r0 + 1;  // row 32 of sX is the hub row: harmless when r1 == nr
-                const float4 *x0 = reinterpret_cast<const float4 *>(sX + r0 * S::RS);
-                const float4 *x1 = reinterpret_cast<const float4 *>(sX + r1 * S::RS);
-                float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+            for (int ch = 0; ch < NCH; ++ch) {
+                if (NCH > 1) {
+                    const float4 *ra = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(idA < 0 ? 0 : idA) * MP) +
+                                       ch * (CHK / 4);
+                    const float4 *rb = reinterpret_cast<const float4 *>(a.L32 + (int64_t)(idB < 0 ? 0 : idB) * MP) +
+                                       ch * (CHK / 4);
 #pragma unroll
-                for (int i4 = 0; i4 < MP / 4; ++i4) {
-                    const float4 u = x0[i4], w = x1[i4];
-                    a0 = __fmaf_rn(u.x, LA[4 * i4 + 0], a0); a1 = __fmaf_rn(w.x, LA[4 * i4 + 0], a1);
-                    b0 = __fmaf_rn(u.x, LB[4 * i4 + 0], b0); b1 = __fmaf_rn(w.x, LB[4 * i4 + 0], b1);
-                    a0 = __fmaf_rn(u.y, LA[4 * i4 + 1], a0); a1 = __fmaf_rn(w.y, LA[4 * i4 + 1], a1);
-                    b0 = __fmaf_rn(u.y, LB[4 * i4 + 1], b0); b1 = __fmaf_rn(w.y, LB[4 * i4 + 1], b1);
-                    a0 = __fmaf_rn(u.z, LA[4 * i4 + 2], a0); a1 = __fmaf_rn(w.z, LA[4 * i4 + 2], a1);
-                    b0 = __fmaf_rn(u.z, LB[4 * i4 + 2], b0); b1 = __fmaf_rn(w.z, LB[4 * i4 + 2], b1);
-                    a0 = __fmaf_rn(u.w, LA[4 * i4 + 3], a0); a1 = __fmaf_rn(w.w, LA[4 * i4 + 3], a1);
-                    b0 = __fmaf_rn(u.w, LB[4 * i4 + 3], b0); b1 = __fmaf_rn(w.w, LB[4 * i4 + 3], b1);
+                    for (int i4 = 0; i4 < CHK / 4; ++i4) {
+                        const float4 ta = (idA >= 0) ? __ldg(ra + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 tb = (idB >= 0) ? __ldg(rb + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        LA[4 * i4 + 0] = ta.x; LA[4 * i4 + 1] = ta.y; LA[4 * i4 + 2] = ta.z; LA[4 * i4 + 3] = ta.w;
+                        LB[4 * i4 + 0] = tb.x; LB[4 * i4 + 1] = tb.y; LB[4 * i4 + 2] = tb.z; LB[4 * i4 + 3] = tb.w;
+                    }
                 }
-                if (cA < K) {
-                    sD[r0 * DS + cA] = a0;
-                    if (r1 < nr) sD[r1 * DS + cA] = a1;
-                }
-                if (cB < K) {
-                    sD[r0 * DS + cB] = b0;
-                    if (r1 < nr) sD[r1 * DS + cB] = b1;
+                for (int r0 = 2 * g; r0 < nr; r0 += 2 * G) {
+                    if (!active) break;
+                    const int r1 = r0 + 1;  // row 32 of sX is the hub row: harmless when r1 == nr
+                    const float4 *x0 = reinterpret_cast<const float4 *>(sX + r0 * S::RS) + ch * (CHK / 4);
+                    const float4 *x1 = reinterpret_cast<const float4 *>(sX + r1 * S::RS) + ch * (CHK / 4);
+                    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+                    if (ch > 0) {  // this lane's own cells of the previous chunk
+                        if (cA < K) {
+                            a0 = sD[r0 * DS + cA];
+                            if (r1 < nr) a1 = sD[r1 * DS + cA];
+                        }
+                        if (cB < K) {
+                            b0 = sD[r0 * DS + cB];
+                            if (r1 < nr) b1 = sD[r1 * DS + cB];
+                        }
+                    }
+#pragma unroll
+                    for (int i4 = 0; i4 < CHK / 4; ++i4) {
+                        const float4 u = x0[i4], w = x1[i4];
+                        a0 = __fmaf_rn(u.x, LA[4 * i4 + 0], a0); a1 = __fmaf_rn(w.x, LA[4 * i4 + 0], a1);
+                        b0 = __fmaf_rn(u.x, LB[4 * i4 + 0], b0); b1 = __fmaf_rn(w.x, LB[4 * i4 + 0], b1);
+                        a0 = __fmaf_rn(u.y, LA[4 * i4 + 1], a0); a1 = __fmaf_rn(w.y, LA[4 * i4 + 1], a1);
+                        b0 = __fmaf_rn(u.y, LB[4 * i4 + 1], b0); b1 = __fmaf_rn(w.y, LB[4 * i4 + 1], b1);
+                        a0 = __fmaf_rn(u.z, LA[4 * i4 + 2], a0); a1 = __fmaf_rn(w.z, LA[4 * i4 + 2], a1);
+                        b0 = __fmaf_rn(u.z, LB[4 * i4 + 2], b0); b1 = __fmaf_rn(w.z, LB[4 * i4 + 2], b1);
+                        a0 = __fmaf_rn(u.w, LA[4 * i4 + 3], a0); a1 = __fmaf_rn(w.w, LA[4 * i4 + 3], a1);
+                        b0 = __fmaf_rn(u.w, LB[4 * i4 + 3], b0); b1 = __fmaf_rn(w.w, LB[4 * i4 + 3], b1);
+                    }
+                    if (cA < K) {
+                        sD[r0 * DS + cA] = a0;
+                        if (r1 < nr) sD[r1 * DS + cA] = a1;
+                    }
+                    if (cB < K) {
+                        sD[r0 * DS + cB] = b0;
+                        if (r1 < nr) sD[r1 * DS + cB] = b1;
+                    }
                 }
             }
             __syncwarp();
             // filter: lane t <-> row t; survivors compacted in place in the row's dots,
             // their column numbers in sJ
             int q = 0;
-            if (lane < nr && rid >= 0) {
+            if (lane < nr && rid >= 0 && (!INC || rnew || any_col_new)) {
                 float *drow = sD + lane * DS;
                 unsigned char *jrow = sJ + lane * K;
                 for (int j = 0; j < K; ++j) {
                     const float d = drow[j];
                     const int cj = sCid[j];
-                    if (cj >= 0 && cj != rid && d >= ph) {
+                    if (cj >= 0 && cj != rid && d >= ph && (!INC || rnew || sCnew[j])) {
                         drow[q] = d;
                         jrow[q] = (unsigned char)j;
                         ++q;
@@ -287,7 +350,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
             // co-friend pair (x in F(v), y = v)
             bool cfpass = false;
             float cfd = 0.f;
-            if (r < K && rid >= 0) {
+            if (r < K && rid >= 0 && (!INC || rnew)) {
                 const float4 *xr = reinterpret_cast<const float4 *>(sX + lane * S::RS);
                 const float4 *lv = reinterpret_cast<const float4 *>(sX + 32 * S::RS);
                 float acc = 0.f;
@@ -372,14 +435,16 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
 
     for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
-        int cid[CPL];
+        int cid[CPL], cnew[CPL];
         double Lc[CPL][MP];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             const int j = lane + 32 * c;
             int id = -1;
+            cnew[c] = 0;
             if (j < K) {
                 id = a.idx[v * K + j];
+                cnew[c] = row_new(a, v, K, 0, j);
                 if (!valid_id(id, n)) {
                     atomicOr(a.err, kErrIndex);
                     id = -1;
@@ -403,9 +468,10 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
         for (int64_t base = 0; base < nrows; base += 32) {
             const int nr = (int)min((int64_t)32, nrows - base);
             const int64_t r = base + lane;
-            int rid = -1;
+            int rid = -1, rnew = 1;
             if (r < nrows) {
                 rid = (r < K) ? a.idx[v * K + r] : a.cof[c0 + (r - K)];
+                rnew = row_new(a, v, K, c0, r);
                 if (!valid_id(rid, n)) {
                     atomicOr(a.err, kErrIndex);
                     rid = -1;
@@ -437,6 +503,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                 const double rnh = __shfl_sync(FULL, nh, rr);
                 const double rtk = __shfl_sync(FULL, tk, rr);
                 const int rik = __shfl_sync(FULL, ik, rr);
+                const int rrnew = __shfl_sync(FULL, rnew, rr);
                 const double2 *xr = reinterpret_cast<const double2 *>(sX + rr * S::RS);
                 double acc[CPL];
 #pragma unroll
@@ -453,7 +520,8 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
                     const double k = rnh - acc[c];
-                    const bool pass = rrid >= 0 && cid[c] >= 0 && cid[c] != rrid && lex_less(k, cid[c], rtk, rik);
+                    const bool pass = rrid >= 0 && cid[c] >= 0 && cid[c] != rrid && (rrnew || cnew[c]) &&
+                                      lex_less(k, cid[c], rtk, rik);
                     const unsigned m = __ballot_sync(FULL, pass);
                     if (lane == rr) mymask[c] = m;
                     sD[(c * 32 + rr) * 33 + lane] = k;
@@ -472,7 +540,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                     acc = __fma_rn(xv.y, lw.y, acc);
                 }
                 cfk = nh - acc;
-                cfpass = lex_less(cfk, (int)v, tk, ik);
+                cfpass = rnew && lex_less(cfk, (int)v, tk, ik);
             }
             int count = cfpass ? 1 : 0;
 #pragma unroll
@@ -535,13 +603,14 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         using S = MixedSmem<MP>;
         const int threads = 128;
         const size_t smem = (size_t)S::warp_bytes(h->K) * (threads / 32);
-        cudaFuncSetAttribute(join_mixed_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto kern = a.flag ? join_mixed_kernel<MP, true> : join_mixed_kernel<MP, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_mixed_kernel<MP>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (per_sm < 1) per_sm = 1;
         const int64_t need = (h->n + threads / 32 - 1) / (threads / 32);
         const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * per_sm);
-        join_mixed_kernel<MP><<<(unsigned)grid, threads, smem, h->stream>>>(a);
+        kern<<<(unsigned)grid, threads, smem, h->stream>>>(a);
     }
     return cudaGetLastError();
 }
@@ -576,6 +645,8 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
     a.err = h->err;
     a.debug = h->prm.debug;
     a.iv = h->iv;
+    a.flag = h->round_flag;
+    a.cof_new = h->round_flag ? h->cof_new : nullptr;
     cudaMemsetAsync(h->bcnt, 0, sizeof(int32_t) * h->n, h->stream);
     h->launches += 1;
     switch (h->MP) {

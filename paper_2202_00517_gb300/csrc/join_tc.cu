@@ -43,6 +43,10 @@ struct TcArgs {
     int32_t *err;
     int debug;
     InstView iv;
+    // incremental proposals (as in join.cu): flags of G_{r-1} and of the coF
+    // entries, or NULL
+    const uint8_t *flag;
+    const uint8_t *cof_new;
     // bound audit (debug)
     const double *X64;
     const double *L64;
@@ -81,7 +85,8 @@ struct TcLayout {
     static constexpr int OFF_BH = A_REGION;
     static constexpr int OFF_BL = OFF_BH + B_BYTES;
     static constexpr int OFF_CID = OFF_BL + B_BYTES;
-    static constexpr int OFF_MISC = OFF_CID + ((N * 4 + 127) & ~127);
+    static constexpr int OFF_CNEW = OFF_CID + ((N * 4 + 127) & ~127);  // new-flags of the columns
+    static constexpr int OFF_MISC = OFF_CNEW + ((N + 127) & ~127);
     static constexpr int BYTES = OFF_MISC + 128;
     static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
 };
@@ -109,6 +114,7 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
     unsigned char *sBh = smem + Lay::OFF_BH;
     unsigned char *sBl = smem + Lay::OFF_BL;
     int *sCid = reinterpret_cast<int *>(smem + Lay::OFF_CID);
+    unsigned char *sCnew = smem + Lay::OFF_CNEW;
     unsigned long long *mbar = reinterpret_cast<unsigned long long *>(smem + Lay::OFF_MISC);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::OFF_MISC + 8);
     int *sAbort = reinterpret_cast<int *>(smem + Lay::OFF_MISC + 16);
@@ -146,8 +152,10 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
         // columns: F(v), then v itself (the co-friend column of the rows of F(v))
         for (int j = t; j < N; j += blockDim.x) {
             int id = -1;
+            int nw = 0;
             if (j < K) {
                 id = a.idx[v * K + j];
+                nw = a.flag ? a.flag[v * K + j] : 1;
                 if (id < 0 || id >= n) {
                     atomicOr(a.err, kErrIndex);
                     id = -1;
@@ -156,6 +164,7 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
                 id = (int)v;
             }
             sCid[j] = id;
+            sCnew[j] = (unsigned char)nw;
         }
         __syncthreads();
         for (int u = t; u < N * (KD / 8); u += blockDim.x) {
@@ -176,9 +185,10 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
         for (int64_t base = 0; base < nrows; base += Lay::M) {
             // rows: thread t <-> row base + t
             const int64_t r = base + t;
-            int rid = -1;
+            int rid = -1, rnew = 1;
             if (r < nrows) {
                 rid = (r < K) ? a.idx[v * K + r] : a.cof[c0 + (r - K)];
+                if (a.flag) rnew = (r < K) ? a.flag[v * K + r] : a.cof_new[c0 + (r - K)];
                 if (rid < 0 || rid >= n) {
                     atomicOr(a.err, kErrIndex);
                     rid = -1;
@@ -277,7 +287,8 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
                         ndot += 1;
                         if (fabs((double)dj - acc) > a.Ex[rid]) nviol += 1;
                     }
-                    if (dj >= ph) {
+                    // incremental: a pair met only through arcs of G_{r-2} is not proposed again
+                    if (dj >= ph && (rnew || sCnew[j])) {
                         drow[q] = dj;
                         sJ[lane * Lay::JS + q] = (unsigned char)j;
                         ++q;
@@ -379,6 +390,8 @@ cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx)
     a.err = h->err;
     a.debug = h->prm.debug;
     a.iv = h->iv;
+    a.flag = h->round_flag;
+    a.cof_new = h->round_flag ? h->cof_new : nullptr;
     a.X64 = h->X64;
     a.L64 = h->L64;
     a.negH = h->negH;

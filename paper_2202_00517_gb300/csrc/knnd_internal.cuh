@@ -168,6 +168,12 @@ struct knnd_handle {
     int32_t *deg;     // n: in-degree, then fill cursor
     int64_t *cof_off; // n+1
     int32_t *cof;     // n*K
+    // incremental proposals (params.incremental): the new-flag of the arc x -> v
+    // of every coF(v) entry; the flags knnd_build keeps when its caller passes
+    // none; the flags of G_{r-1} during a round (NULL: every pair is proposed)
+    uint8_t *cof_new;   // n*K
+    uint8_t *flag_tmp;  // n*K
+    const uint8_t *round_flag;
     int64_t *scan_tmp;
     int64_t scan_tmp_len;
     // per-row thresholds of the join filter

@@ -6,6 +6,9 @@
   the same update count and the same clustering hits;
 * free-running builds: identical rounds, updates, hits and graphs;
 * the mixed form equals the FP64 form bit for bit;
+* incremental proposals (a pair met only through arcs of the previous round's
+  graph is not proposed again) give the same graph as proposing every pair;
+  lockstep rounds run both ways against the oracle's full pool;
 * shapes spanning several warps/tiles with ragged tails, K from 2 to 64, m from
   1 (every key ties) to 128, n = K+1, duplicated points (exact ties).
 """
@@ -34,10 +37,10 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000):
+def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000, incremental=True):
     n, m = pts.shape
     p = _dev(pts)
-    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, fcc_samples=S)
+    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, fcc_samples=S, incremental=incremental)
     pts64 = pts.astype(np.float64)
     gi, gk, _ = h.init_graph(p, seed)
     ri, rk = oracle.init_graph(pts64, K, seed)
@@ -46,10 +49,11 @@ def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000):
     upd = torch.zeros(1, dtype=torch.int64, device="cuda")
     hits = torch.zeros(1, dtype=torch.int64, device="cuda")
     total_ties = 0
+    rf = np.ones(ri.shape, dtype=np.uint8)  # new-flags of the oracle's graph (read when incremental)
     for r in range(1, rounds + 1):
         idx = _dev(ri)
         key = _dev(rk)
-        flag = torch.empty_like(idx, dtype=torch.uint8)
+        flag = _dev(rf)
         h.round(None, seed, r, idx, key, flag, upd, hits)
         h.sync()
         ni, nk, nf, nu, _ = oracle.round_(pts64, ri)
@@ -61,7 +65,7 @@ def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000):
             assert int(upd.item()) == nu
             assert int(hits.item()) == oracle.fcc(ni, seed, r, S)
         check_invariants(idx.cpu().numpy(), key.cpu().numpy())
-        ri, rk = ni, nk
+        ri, rk, rf = ni, nk, nf
     h.close()
     return total_ties
 
@@ -103,6 +107,7 @@ SHAPES = [
     (1500, 65, 32, 7, "f32"),
     (600, 128, 64, 8, "f64"),
     (2500, 24, 20, 9, "f32"),
+    (1200, 40, 17, 10, "f32"),   # 40 coordinates (48 padded), odd K
 ]
 
 
@@ -130,6 +135,31 @@ def test_duplicated_points_exact_ties(knnd, prec):
     h.close()
     assert out["rounds"] == ref["rounds"] and out["updates"] == list(ref["updates"])
     assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lockstep_all_pairs_proposed(knnd, prec):
+    # incremental proposals off: every pair the tiles meet goes to the merge
+    pts = dirichlet_points(3000, 11, 12, np.float32)
+    assert _lockstep(knnd, pts, 12, 12, prec, rounds=4, dtype="f32", S=500, incremental=False) <= 6
+
+
+@pytest.mark.parametrize("n,m,K", [(100_000, 21, 20), (30_000, 65, 32), (20_000, 6, 8)])
+def test_incremental_proposals_same_graph(knnd, n, m, K):
+    # a pair met only through arcs of the previous round's graph is not proposed
+    # again: the build is the same, bit for bit, with fewer candidates merged
+    seed = 4
+    pts = _dev(dirichlet_points(n, m, seed, np.float32))
+    for prec in PRECS:
+        res = {}
+        for inc in (False, True):
+            h = knnd.Handle(n, m, K, dtype="f32", precision=prec, incremental=inc)
+            res[inc] = h.build(pts, seed)
+            h.close()
+        a, b = res[False], res[True]
+        assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"], prec
+        assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["key"], b["key"]), prec
+        assert b["join_survivors"] < a["join_survivors"], prec
 
 
 @pytest.mark.parametrize("n,m,K", [(200_000, 21, 20), (60_000, 65, 32)])
