@@ -415,19 +415,98 @@ struct LaneTop {
     }
 };
 
-__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v)
+// Per-warp scratch of the batched insertion (K <= 32).
+struct BatchScratch {
+    uint64_t xk[32], ck[32], mk[32];
+    int xi[32], ci[32], mi[32], mo[32];
+};
+
+// Inserts up to 32 candidates at once (one per lane: key k, index ci, when
+// `has`) into the sorted list X of K <= 32 entries: candidates that cannot
+// beat the K-th entry are dropped; the rest are sorted by (key, index) with a
+// warp bitonic network, copies of one candidate and copies of listed entries
+// are dropped, and each entry's place in the merged list is its own index
+// plus its rank in the other list (binary search in shared memory).  Same
+// result as offering the candidates one by one.
+__device__ __forceinline__ void insert_batch(WarpList<1> &X, int K, int lane, uint64_t k, int ci, bool has,
+                                             uint64_t &xk, int &xi, BatchScratch &sb)
 {
+    const unsigned FULL = 0xffffffffu;
+    bool v = has && lex_less_u(k, ci, xk, xi);
+    if (!__any_sync(FULL, v)) return;
+    uint64_t ck = v ? k : ~0ull;
+    int cj = v ? ci : 0x7fffffff;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t t = __shfl_xor_sync(0xffffffffu, v, o);
-        v = t < v ? t : v;
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            const uint64_t ok = __shfl_xor_sync(FULL, ck, j);
+            const int oj = __shfl_xor_sync(FULL, cj, j);
+            const bool keep_min = ((lane & kk) == 0) == ((lane & j) == 0);
+            const bool take = keep_min ? lex_less_u(ok, oj, ck, cj) : lex_less_u(ck, cj, ok, oj);
+            if (take) {
+                ck = ok;
+                cj = oj;
+            }
+        }
     }
-    return v;
+    const int pj = __shfl_up_sync(FULL, cj, 1);
+    v = ck != ~0ull && !(lane > 0 && pj == cj);  // one index, one key: copies are adjacent
+    if (lane < K) {
+        sb.xk[lane] = X.k[0];
+        sb.xi[lane] = X.i[0];
+    }
+    __syncwarp();
+    int rc = 0;  // listed entries before the candidate
+    if (v) {
+        int lo = 0, hi = K;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (lex_less_u(sb.xk[mid], sb.xi[mid], ck, cj)) lo = mid + 1;
+            else hi = mid;
+        }
+        rc = lo;
+        if (lo < K && sb.xi[lo] == cj) v = false;  // already listed
+    }
+    const unsigned vm = __ballot_sync(FULL, v);
+    const int L = __popc(vm), cpos = __popc(vm & lanemask_lt());
+    if (v) {
+        sb.ck[cpos] = ck;
+        sb.ci[cpos] = cj;
+    }
+    __syncwarp();
+    if (lane < K) {  // listed entry: its index plus the candidates before it
+        int lo = 0, hi = L;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (lex_less_u(sb.ck[mid], sb.ci[mid], X.k[0], X.i[0])) lo = mid + 1;
+            else hi = mid;
+        }
+        const int pos = lane + lo;
+        if (pos < K) {
+            sb.mk[pos] = X.k[0];
+            sb.mi[pos] = X.i[0];
+            sb.mo[pos] = X.old[0];
+        }
+    }
+    if (v && cpos + rc < K) {
+        sb.mk[cpos + rc] = ck;
+        sb.mi[cpos + rc] = cj;
+        sb.mo[cpos + rc] = 0;
+    }
+    __syncwarp();
+    if (lane < K) {
+        X.k[0] = sb.mk[lane];
+        X.i[0] = sb.mi[lane];
+        X.old[0] = sb.mo[lane];
+    }
+    __syncwarp();
+    X.kth(K, xk, xi);
 }
 
 template <int NE, int R, bool MIXED>
 __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &X, const int *tab, int2 *live_list,
-                         int64_t base, int cnt, const Bounds<MIXED> &B, long long &rescored)
+                         int64_t base, int cnt, const Bounds<MIXED> &B, long long &rescored, BatchScratch &sb)
 {
     const int K = a.K;
     LaneTop<R> L;
@@ -452,22 +531,25 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
     X.kth(K, T0, Ti);
     double T = from_dkey(T0);
     if (P > 32) {
+        // the K smallest distinct (u, index) among the lanes' lists, one per step:
+        // the warp minimum of the heads by u, then by index (two single-instruction
+        // warp reductions); every lane holding that candidate pops it (copies of one
+        // candidate sit in different lanes, never twice in one)
         int popped = 0, count = 0;
-        uint64_t prev = ~0ull, m = ~0ull;
+        uint32_t mu = 0xffffffffu;
         while (count < K) {
             uint64_t head = ~0ull;
 #pragma unroll
             for (int r = 0; r < R; ++r)
                 if (r == popped) head = L.pk[r];
-            m = warp_min_u64(head);
-            if (m == ~0ull) break;
-            const int win = __ffs(__ballot_sync(0xffffffffu, head == m)) - 1;
-            if (lane == win) popped += 1;
-            if (m == prev) continue;
-            prev = m;
+            const uint32_t hu = (uint32_t)(head >> 32), hi = (uint32_t)head;
+            mu = __reduce_min_sync(0xffffffffu, hu);
+            if (mu == 0xffffffffu) break;  // every list exhausted
+            const uint32_t mi = __reduce_min_sync(0xffffffffu, hu == mu ? hi : 0xffffffffu);
+            if (hu == mu && hi == mi) popped += 1;
             count += 1;
         }
-        if (count == K) T = fmin(T, B.upper(from_sortable_bits((uint32_t)(m >> 32))));
+        if (count == K) T = fmin(T, B.upper(from_sortable_bits(mu)));
     }
     const uint32_t reach = sortable_bits(B.u_reach(T));
     if (__any_sync(0xffffffffu, L.drop <= reach)) return false;
@@ -499,11 +581,15 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
                 k = dkey(a.bkey[base + e.y]);
             }
         }
-        unsigned mask = __ballot_sync(0xffffffffu, has);
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            X.offer(K, lane, __shfl_sync(0xffffffffu, k, src), __shfl_sync(0xffffffffu, ci, src), xk, xi);
+        if constexpr (NE == 1) {
+            insert_batch(X, K, lane, k, ci, has, xk, xi, sb);
+        } else {
+            unsigned mask = __ballot_sync(0xffffffffu, has);
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                X.offer(K, lane, __shfl_sync(0xffffffffu, k, src), __shfl_sync(0xffffffffu, ci, src), xk, xi);
+            }
         }
     }
     __syncwarp();
@@ -515,6 +601,7 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
 {
     __shared__ int s_hash[8][kHashSlots];
     __shared__ int2 s_live[8][32 * R];
+    __shared__ BatchScratch s_batch[NE == 1 ? 8 : 1];
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int K = a.K;
@@ -534,7 +621,8 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
             B.nh = MIXED ? a.negH[x] : 0.0;
             B.E = MIXED ? a.Ex[x] : 0.0;
             hash_fill(tab, lane, K, X);
-            if (!fast_row<NE, R, MIXED>(a, x, lane, X, tab, live_list, base, cnt, B, rescored)) {
+            if (!fast_row<NE, R, MIXED>(a, x, lane, X, tab, live_list, base, cnt, B, rescored,
+                                        s_batch[NE == 1 ? (threadIdx.x >> 5) : 0])) {
                 // the row stays as it is here; merge_fallback_kernel finishes it
                 if (lane == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)x;
                 fallbacks += 1;
