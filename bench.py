@@ -283,7 +283,7 @@ def gpu_single(args, name, rank, world, local, barrier):
         "join_survivors_per_build": info["join_survivors"],
         "phase_ms_per_build": {p: st["phase_ms"][p] / steps for p in st["phase_ms"]},
         "phase_share": {p: st["phase_ms"][p] / total_ph for p in st["phase_ms"]},
-        "roofline": {"kernel": f"join_mixed_kernel<{MP}>" if args.form == "mixed" else f"join_tc_kernel<{MP}>",
+        "roofline": {"kernel": f"join_mixed_kernel<{MP}, 0>" if args.form == "mixed" else f"join_tc_kernel<{MP}>",
                      "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
@@ -355,7 +355,7 @@ def gpu_batch(args, rank, world, local, barrier):
         key = torch.empty((n, k), dtype=torch.float64, device=dev)
         outs.append((idx, key))
         arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, k, seeds[i], idx.data_ptr(), key.data_ptr())
-    prm = _lib.knnd_params(10000, 64, 1, 0, 0, 0)
+    prm = _lib.knnd_params(10000, 64, 1, 0, 0, 0, 0.0)
     b = ctypes.c_void_p()
     st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     _lib.check(lib.knnd_batch_create(ctypes.byref(b), count, ctypes.cast(arr, ctypes.c_void_p), _lib.KNND_F32,

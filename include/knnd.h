@@ -81,12 +81,15 @@ typedef struct {
     int32_t timing;               /* 1: CUDA events around every phase, see knnd_stats (0) */
     int32_t incremental;          /* 1: a round does not propose again a pair it met only through edges
                                      of the previous round's graph (0); see knnd_round */
+    float stop_delta;             /* > 0: also stop after a round with fewer than stop_delta * n * K
+                                     updates, Dong et al.'s delta-proportion rule (Sec. 2, Table 1) (0) */
 } knnd_params;
 
 /* Why knnd_build stopped. */
 #define KNND_STOP_FCC 1        /* clustering hits did not increase (Sec. 3.3 (iv)) */
 #define KNND_STOP_ZERO 2       /* a round made no update */
 #define KNND_STOP_MAX_ROUNDS 3 /* max_rounds reached */
+#define KNND_STOP_DELTA 4      /* fewer than stop_delta * n * K updates (params.stop_delta) */
 
 /* Per-build report, filled by knnd_build / knnd_build_host (host memory). */
 typedef struct {

@@ -420,13 +420,16 @@ int64_t orc_fcc(const int32_t *idx, int64_t n, int K, uint64_t seed, int32_t rou
 /* ------------------------------------------------------------------------ */
 /* The build loop (Sec. 3; Sec. 4.2): initial graph, then rounds until the   */
 /* friend clustering hit count does not increase (Sec. 3.3 (iv)), or a round */
-/* makes no update (when stop_on_zero), or max_rounds rounds.  Returns the   */
+/* makes no update (when stop_on_zero), or (stop_delta > 0) a round makes   */
+/* fewer than stop_delta * n * K updates, the delta-proportion rule of Dong  */
+/* et al. that Sec. 2 (Table 1, item (b)) contrasts with the statistical     */
+/* stop, or max_rounds rounds.  Returns the                                  */
 /* number of rounds performed; updates[r-1] is round r's update count and    */
 /* hits[r] the clustering hits of the graph after round r (hits[0]: initial  */
 /* graph).  proposals (optional) receives the total candidate multiset size. */
 /* ------------------------------------------------------------------------ */
 int32_t orc_build(const double *pts, int64_t n, int m, int K, uint64_t seed, int32_t S,
-                  int32_t max_rounds, int32_t stop_on_zero, int32_t *idx, double *key,
+                  int32_t max_rounds, int32_t stop_on_zero, double stop_delta, int32_t *idx, double *key,
                   int64_t *updates, int64_t *hits, int64_t *proposals)
 {
     int32_t *nidx = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * (size_t)K);
@@ -446,6 +449,7 @@ int32_t orc_build(const double *pts, int64_t n, int m, int K, uint64_t seed, int
         hits[r] = orc_fcc(idx, n, K, seed, r, S);
         if (hits[r] <= hits[r - 1]) break;
         if (stop_on_zero && updates[r - 1] == 0) break;
+        if (stop_delta > 0.0 && (double)updates[r - 1] < stop_delta * (double)n * (double)K) break;
     }
     if (proposals) *proposals = props_total;
     free(nidx);

@@ -66,7 +66,8 @@ def _load():
             "orc_pools": (None, [P, i64, ctypes.c_int, i64, i64, P, P]),
             "orc_indegree": (None, [P, i64, ctypes.c_int, P]),
             "orc_fcc": (i64, [P, i64, ctypes.c_int, u64, i32, i32]),
-            "orc_build": (i32, [P, i64, ctypes.c_int, ctypes.c_int, u64, i32, i32, i32, P, P, P, P, P]),
+            "orc_build": (i32, [P, i64, ctypes.c_int, ctypes.c_int, u64, i32, i32, i32, ctypes.c_double,
+                                P, P, P, P, P]),
             "orc_bruteforce": (None, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P]),
             "orc_diameter_exact": (i32, [P, i64, ctypes.c_int]),
             "orc_diameter_bounds": (None, [P, i64, ctypes.c_int, i32, u64, P, P]),
@@ -198,8 +199,10 @@ def fcc(idx, seed: int, round_no: int, S: int) -> int:
     return int(_load().orc_fcc(_p(g), n, K, seed, round_no, S))
 
 
-def build(points, K: int, seed: int, S: int = 10000, max_rounds: int = 64, stop_on_zero: bool = True):
-    """Full build: returns dict(idx, key, rounds, updates[rounds], hits[rounds+1], proposals)."""
+def build(points, K: int, seed: int, S: int = 10000, max_rounds: int = 64, stop_on_zero: bool = True,
+          stop_delta: float = 0.0):
+    """Full build: returns dict(idx, key, rounds, updates[rounds], hits[rounds+1], proposals).
+    stop_delta > 0: also stop after a round with fewer than stop_delta*n*K updates."""
     p = _pts(points)
     n, m = p.shape
     idx = np.zeros((n, K), dtype=np.int32)
@@ -207,7 +210,7 @@ def build(points, K: int, seed: int, S: int = 10000, max_rounds: int = 64, stop_
     upd = np.zeros(max_rounds, dtype=np.int64)
     hits = np.zeros(max_rounds + 1, dtype=np.int64)
     props = np.zeros(1, dtype=np.int64)
-    r = _load().orc_build(_p(p), n, m, K, seed, S, max_rounds, int(stop_on_zero), _p(idx), _p(key),
+    r = _load().orc_build(_p(p), n, m, K, seed, S, max_rounds, int(stop_on_zero), float(stop_delta), _p(idx), _p(key),
                           _p(upd), _p(hits), _p(props))
     return {"idx": idx, "key": key, "rounds": int(r), "updates": upd[:r].copy(),
             "hits": hits[:r + 1].copy(), "proposals": int(props[0])}

@@ -32,6 +32,7 @@ KNND_MAX_ROUNDS = 64
 KNND_STOP_FCC = 1
 KNND_STOP_ZERO = 2
 KNND_STOP_MAX_ROUNDS = 3
+KNND_STOP_DELTA = 4
 
 EXPORTS = [
     "knnd_create", "knnd_destroy", "knnd_set_stream", "knnd_prepare", "knnd_init_graph", "knnd_round",
@@ -46,7 +47,7 @@ KNND_NOALLOC_MAX_SAMPLES = 1 << 20
 class knnd_params(ctypes.Structure):
     _fields_ = [("fcc_samples", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("stop_on_zero_updates", ctypes.c_int32), ("debug", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("incremental", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("incremental", ctypes.c_int32), ("stop_delta", ctypes.c_float)]
 
 
 class knnd_build_info(ctypes.Structure):

@@ -161,6 +161,7 @@ knnd_params default_params()
     p.debug = 0;
     p.timing = 0;
     p.incremental = 0;
+    p.stop_delta = 0.f;
     return p;
 }
 
@@ -307,6 +308,7 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     knnd_params prm = params ? *params : knnd::default_params();
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
     if (prm.incremental != 0 && prm.incremental != 1) return KNND_EINVAL;
+    if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
     // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
     if ((int64_t)K * K + (int64_t)(K + 1) * (n - 1) >= ((int64_t)1 << 31)) return KNND_EOVERFLOW;
     knnd::Caps caps;
@@ -438,6 +440,11 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
         }
         if (h->prm.stop_on_zero_updates && info->updates[r - 1] == 0) {
             info->stop_reason = KNND_STOP_ZERO;
+            break;
+        }
+        if (h->prm.stop_delta > 0.f &&
+            (double)info->updates[r - 1] < (double)h->prm.stop_delta * (double)h->n * (double)h->K) {
+            info->stop_reason = KNND_STOP_DELTA;
             break;
         }
     }

@@ -67,7 +67,7 @@ __global__ void record_hits0_kernel(InstView iv, int32_t ninst, History hs, int3
 // After round r: per-instance stop decision of Sec. 3.3 (iv) (hits of round r
 // not above those of round r-1), or no update, or the round cap.
 __global__ void stop_kernel(InstView iv, int32_t *active, int32_t ninst, History hs, int32_t r, int32_t max_rounds,
-                            int32_t stop_on_zero)
+                            int32_t stop_on_zero, float stop_delta, int32_t K)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ninst || !active[i]) return;
@@ -81,6 +81,7 @@ __global__ void stop_kernel(InstView iv, int32_t *active, int32_t ninst, History
     int reason = 0;
     if (hits <= h[r - 1]) reason = KNND_STOP_FCC;
     else if (stop_on_zero && upd == 0) reason = KNND_STOP_ZERO;
+    else if (stop_delta > 0.f && (double)upd < (double)stop_delta * (double)iv.n[i] * (double)K) reason = KNND_STOP_DELTA;
     else if (r == max_rounds) reason = KNND_STOP_MAX_ROUNDS;
     if (reason) {
         active[i] = 0;
@@ -256,7 +257,7 @@ knnd_status run_sub(knnd_batch *b, const SubBatch &sb, knnd_build_info *info)
         e = launch_fcc_batch(h, b->idx, r);
         if (e) return status_of(e);
         stop_kernel<<<(ni + T - 1) / T, T, 0, st>>>(h->iv, h->inst_active, ni, b->hs, r, R,
-                                                    b->prm.stop_on_zero_updates);
+                                                    b->prm.stop_on_zero_updates, b->prm.stop_delta, sb.K);
         h->launches += 1;
         e = cudaMemcpyAsync(b->h_nactive, b->hs.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaStreamSynchronize(st);
@@ -312,6 +313,7 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
     knnd_params prm = params ? *params : default_params();
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
     if (prm.incremental != 0 && prm.incremental != 1) return KNND_EINVAL;
+    if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
     if (prm.timing) prm.timing = 0;  // phase timing is a single-instance feature
     const bool mixed = precision != KNND_PREC_FP64;
     for (int32_t i = 0; i < count; ++i) {

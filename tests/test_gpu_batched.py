@@ -76,3 +76,22 @@ def test_batched_rejects_bad_instances():
     with pytest.raises(_lib.KnndError) as e:
         knnd.build_batched([p, q], [3, 3], [1, 2])
     assert e.value.status == _lib.KNND_EDOMAIN
+
+
+def test_batched_delta_stop_equals_separate_builds():
+    import paper_2202_00517_gb300 as knnd
+    shapes = _mix(24, 9)
+    pts = [torch.from_numpy(dirichlet_points(n, m, 500 + i, np.float32)).cuda() for i, (n, m, K) in enumerate(shapes)]
+    Ks = [K for _, _, K in shapes]
+    seeds = [0x5EED0100 + i for i in range(len(shapes))]
+    res = knnd.build_batched(pts, Ks, seeds, fcc_samples=700, stop_delta=0.02)
+    reasons = set()
+    for i, (n, m, K) in enumerate(shapes):
+        h = knnd.Handle(n, m, K, dtype="f32", fcc_samples=700, stop_delta=0.02)
+        ref = h.build(pts[i], seeds[i])
+        h.close()
+        b = res[i]
+        assert b["rounds"] == ref["rounds"] and b["stop_reason"] == ref["stop_reason"], i
+        assert b["updates"] == ref["updates"] and torch.equal(b["idx"], ref["idx"]), i
+        reasons.add(b["stop_reason"])
+    assert knnd.api._lib.KNND_STOP_DELTA in reasons

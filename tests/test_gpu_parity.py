@@ -231,3 +231,19 @@ def test_out_of_range_indices_are_reported(knnd):
     assert e.value.status == knnd.api._lib.KNND_EINVAL
     h.sync()  # cleared
     h.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_delta_proportion_stop_matches_oracle(knnd, prec):
+    n, m, K, seed, S = 3000, 6, 10, 21, 2000
+    pts = dirichlet_points(n, m, seed, np.float64)
+    ref_full = oracle.build(pts, K, seed, S=S)
+    delta = (ref_full["updates"][2] + 0.5) / (n * K)
+    ref = oracle.build(pts, K, seed, S=S, stop_delta=delta)
+    h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, stop_delta=delta)
+    out = h.build(_dev(pts), seed)
+    h.close()
+    assert out["rounds"] == ref["rounds"] == 3
+    assert out["stop_reason"] == knnd.api._lib.KNND_STOP_DELTA
+    assert out["updates"] == list(ref["updates"]) and out["fcc_hits"] == list(ref["hits"])
+    assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])

@@ -74,3 +74,23 @@ def test_config1_rounds_within_twice_diameter():
     assert h[-1] <= h[-2]
     assert np.array_equal(res["idx"], oracle.build(p, K, seed)["idx"])
     assert _recall(p, res, K) >= 0.9
+
+
+def test_delta_proportion_stop_truncates_the_build():
+    # Dong et al.'s rule (Sec. 2, Table 1 item (b)): stop after the first round with
+    # fewer than delta*n*K updates.  The build is the same sequence of graphs cut at
+    # that round: it equals the build capped at the same number of rounds.
+    n, m, K, seed = 2000, 6, 10, 0
+    p = dirichlet_points(n, m, seed, np.float64)
+    full = oracle.build(p, K, seed, S=2000, stop_on_zero=False)
+    upd = full["updates"]
+    r_stop = 3
+    delta = (upd[r_stop - 1] + 0.5) / (n * K)  # round 3 is the first below the line
+    assert all(u >= delta * n * K for u in upd[:r_stop - 1])
+    d = oracle.build(p, K, seed, S=2000, stop_on_zero=False, stop_delta=delta)
+    assert d["rounds"] == r_stop
+    assert list(d["updates"]) == list(upd[:r_stop])
+    cut = oracle.build(p, K, seed, S=2000, stop_on_zero=False, max_rounds=r_stop)
+    assert np.array_equal(d["idx"], cut["idx"]) and np.array_equal(d["key"], cut["key"])
+    # delta = 0 is off
+    assert oracle.build(p, K, seed, S=2000, stop_on_zero=False, stop_delta=0.0)["rounds"] == full["rounds"]
