@@ -157,11 +157,24 @@ void orc_logs(const double *pts, int64_t n, int m, double *L, double *negH)
     }
 }
 
+/* Direction of the comparator.  0 (the paper's, Sec. 2.2, Sec. 4.4): x ranks
+ * y by D(x||y) = key(x, y).  1 (a variant: the divergence is asymmetric, and
+ * the comparator is any function of x, Sec. 2 item (a)): x ranks y by
+ * D(y||x) = key(y, x).  Set before the calls that key pairs. */
+static int orc_dir = 0;
+
+void orc_set_direction(int32_t reverse) { orc_dir = reverse ? 1 : 0; }
+
 /* key(x, y) = negH(x) - sum_i x_i * log(y_i), the inner sum an fma chain
- * from 0 over i = 0..m-1. */
+ * from 0 over i = 0..m-1; in the reverse direction the two roles swap. */
 static double orc_key_from_tables(const double *pts, const double *L, const double *negH,
                                   int m, int64_t x, int64_t y)
 {
+    if (orc_dir) {
+        const int64_t t = x;
+        x = y;
+        y = t;
+    }
     double dot = 0.0;
     for (int i = 0; i < m; ++i) dot = fma(pts[x * m + i], L[y * m + i], dot);
     return negH[x] - dot;

@@ -66,6 +66,7 @@ def _load():
             "orc_pools": (None, [P, i64, ctypes.c_int, i64, i64, P, P]),
             "orc_indegree": (None, [P, i64, ctypes.c_int, P]),
             "orc_fcc": (i64, [P, i64, ctypes.c_int, u64, i32, i32]),
+            "orc_set_direction": (None, [i32]),
             "orc_build": (i32, [P, i64, ctypes.c_int, ctypes.c_int, u64, i32, i32, i32, ctypes.c_double,
                                 P, P, P, P, P]),
             "orc_bruteforce": (None, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P]),
@@ -79,6 +80,25 @@ def _load():
             f.argtypes = args
         _lib = lib
         return lib
+
+
+_dir_lock = threading.Lock()
+
+
+class _direction:
+    """Comparator direction for the calls inside: reverse=True ranks y for x by
+    D(y||x) instead of D(x||y)."""
+
+    def __init__(self, reverse: bool):
+        self.reverse = bool(reverse)
+
+    def __enter__(self):
+        _dir_lock.acquire()
+        _load().orc_set_direction(int(self.reverse))
+
+    def __exit__(self, *exc):
+        _load().orc_set_direction(0)
+        _dir_lock.release()
 
 
 def _p(a: np.ndarray):
@@ -130,28 +150,31 @@ def logs(points):
     return L, negH
 
 
-def keys_pairs(points, xs, ys) -> np.ndarray:
-    """Canonical FP64 key(x, y) = negH(x) - <x, log y> for each pair."""
+def keys_pairs(points, xs, ys, reverse: bool = False) -> np.ndarray:
+    """Canonical FP64 key(x, y) = negH(x) - <x, log y> for each pair (reverse:
+    key(y, x), the rank of y for x by D(y||x))."""
     p = _pts(points)
     n, m = p.shape
     xs = np.ascontiguousarray(xs, dtype=np.int32)
     ys = np.ascontiguousarray(ys, dtype=np.int32)
     out = np.zeros(len(xs))
-    _load().orc_keys_pairs(_p(p), n, m, _p(xs), _p(ys), len(xs), _p(out))
+    with _direction(reverse):
+        _load().orc_keys_pairs(_p(p), n, m, _p(xs), _p(ys), len(xs), _p(out))
     return out
 
 
-def init_graph(points, K: int, seed: int):
+def init_graph(points, K: int, seed: int, reverse: bool = False):
     """Initial random K-out graph (idx n x K int32, key n x K float64), rows sorted."""
     p = _pts(points)
     n, m = p.shape
     idx = np.zeros((n, K), dtype=np.int32)
     key = np.zeros((n, K))
-    _load().orc_init_graph(_p(p), n, m, K, seed, _p(idx), _p(key))
+    with _direction(reverse):
+        _load().orc_init_graph(_p(p), n, m, K, seed, _p(idx), _p(key))
     return idx, key
 
 
-def round_(points, idx_in, x0: int = 0, x1: int | None = None):
+def round_(points, idx_in, x0: int = 0, x1: int | None = None, reverse: bool = False):
     """One synchronous round from graph idx_in.  Rows [x0, x1) are computed.
 
     Returns (idx, key, newflag, updates, proposals); rows outside [x0, x1) of
@@ -166,7 +189,8 @@ def round_(points, idx_in, x0: int = 0, x1: int | None = None):
     key = np.zeros((n, K))
     flag = np.zeros((n, K), dtype=np.uint8)
     props = np.zeros(1, dtype=np.int64)
-    upd = _load().orc_round(_p(p), n, m, K, _p(g), x0, x1, _p(idx), _p(key), _p(flag), _p(props))
+    with _direction(reverse):
+        upd = _load().orc_round(_p(p), n, m, K, _p(g), x0, x1, _p(idx), _p(key), _p(flag), _p(props))
     return idx, key, flag, int(upd), int(props[0])
 
 
@@ -200,7 +224,7 @@ def fcc(idx, seed: int, round_no: int, S: int) -> int:
 
 
 def build(points, K: int, seed: int, S: int = 10000, max_rounds: int = 64, stop_on_zero: bool = True,
-          stop_delta: float = 0.0):
+          stop_delta: float = 0.0, reverse: bool = False):
     """Full build: returns dict(idx, key, rounds, updates[rounds], hits[rounds+1], proposals).
     stop_delta > 0: also stop after a round with fewer than stop_delta*n*K updates."""
     p = _pts(points)
@@ -210,20 +234,22 @@ def build(points, K: int, seed: int, S: int = 10000, max_rounds: int = 64, stop_
     upd = np.zeros(max_rounds, dtype=np.int64)
     hits = np.zeros(max_rounds + 1, dtype=np.int64)
     props = np.zeros(1, dtype=np.int64)
-    r = _load().orc_build(_p(p), n, m, K, seed, S, max_rounds, int(stop_on_zero), float(stop_delta), _p(idx), _p(key),
-                          _p(upd), _p(hits), _p(props))
+    with _direction(reverse):
+        r = _load().orc_build(_p(p), n, m, K, seed, S, max_rounds, int(stop_on_zero), float(stop_delta), _p(idx),
+                              _p(key), _p(upd), _p(hits), _p(props))
     return {"idx": idx, "key": key, "rounds": int(r), "updates": upd[:r].copy(),
             "hits": hits[:r + 1].copy(), "proposals": int(props[0])}
 
 
-def bruteforce(points, K: int, queries=None):
+def bruteforce(points, K: int, queries=None, reverse: bool = False):
     """Exact K-NN lists (by (key, idx)) of the query points."""
     p = _pts(points)
     n, m = p.shape
     q = np.arange(n, dtype=np.int32) if queries is None else np.ascontiguousarray(queries, dtype=np.int32)
     idx = np.zeros((len(q), K), dtype=np.int32)
     key = np.zeros((len(q), K))
-    _load().orc_bruteforce(_p(p), n, m, K, _p(q), len(q), _p(idx), _p(key))
+    with _direction(reverse):
+        _load().orc_bruteforce(_p(p), n, m, K, _p(q), len(q), _p(idx), _p(key))
     return idx, key
 
 

@@ -16,7 +16,9 @@ import oracle
 from paper_2202_00517_gb300.datagen import dirichlet_points
 
 
-def _scipy_keys(p, x, ys):
+def _scipy_keys(p, x, ys, reverse=False):
+    if reverse:  # y ranked for x by D(y||x)
+        return rel_entr(p[ys], p[x][None, :]).sum(1)
     return rel_entr(p[x][None, :], p[ys]).sum(1)
 
 
@@ -77,18 +79,19 @@ def _python_pool(idx, x):
     return pool
 
 
-def test_round_equals_independent_pool_topk():
+@pytest.mark.parametrize("reverse", [False, True])
+def test_round_equals_independent_pool_topk(reverse):
     n, m, K = 80, 4, 5
     p = dirichlet_points(n, m, 21, np.float64)
-    idx0, _ = oracle.init_graph(p, K, 21)
+    idx0, _ = oracle.init_graph(p, K, 21, reverse=reverse)
     pools = oracle.pools(idx0)
-    idx1, key1, flag, upd, props = oracle.round_(p, idx0)
+    idx1, key1, flag, upd, props = oracle.round_(p, idx0, reverse=reverse)
     _check_rows(idx1, key1, n, K)
     newcount = 0
     for x in range(n):
         pool = sorted(_python_pool(idx0, x))
         assert np.array_equal(pools[x], np.array(pool)), x
-        keys = _scipy_keys(p, x, np.array(pool))
+        keys = _scipy_keys(p, x, np.array(pool), reverse)
         order = np.lexsort((np.array(pool), keys))
         best = np.array(pool)[order[:K]]
         kb = keys[order[:K + 1]]
@@ -151,11 +154,14 @@ def test_round_row_range():
 
 
 # ---------------------------------------------------------------- brute force
-def test_bruteforce_matches_full_matrix():
+@pytest.mark.parametrize("reverse", [False, True])
+def test_bruteforce_matches_full_matrix(reverse):
     n, m, K = 300, 6, 9
     p = dirichlet_points(n, m, 13, np.float64)
-    bi, bk = oracle.bruteforce(p, K)
-    D = rel_entr(p[:, None, :], p[None, :, :]).sum(-1)
+    bi, bk = oracle.bruteforce(p, K, reverse=reverse)
+    D = rel_entr(p[:, None, :], p[None, :, :]).sum(-1)  # D[x, y] = D(x||y)
+    if reverse:
+        D = D.T.copy()  # row x: D(y||x)
     np.fill_diagonal(D, np.inf)
     for x in range(n):
         order = np.lexsort((np.arange(n), D[x]))[:K]

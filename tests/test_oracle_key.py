@@ -87,3 +87,19 @@ def test_logs_table():
     L, negH = oracle.logs(p)
     assert np.array_equal(L, np.log(p))
     assert np.allclose(negH, (p * np.log(p)).sum(1), rtol=1e-14, atol=0)
+
+
+def test_reverse_direction_matches_scipy():
+    # the variant comparator ranks y for x by D(y||x) (scipy: rel_entr(y, x))
+    p = dirichlet_points(300, 11, 6, np.float64)
+    rng = np.random.default_rng(1)
+    xs = rng.integers(0, 300, 3000)
+    ys = rng.integers(0, 300, 3000)
+    k = oracle.keys_pairs(p, xs, ys, reverse=True)
+    ref = rel_entr(p[ys], p[xs]).sum(axis=1)
+    scale = np.abs((p[ys] * np.log(p[ys])).sum(1)) + (p[ys] * np.abs(np.log(p[xs]))).sum(1)
+    assert np.all(np.abs(k - ref) <= 1e-13 * scale)
+    # the two directions differ (the divergence is not symmetric) but agree on x = y
+    assert np.max(np.abs(k - oracle.keys_pairs(p, xs, ys))) > 1e-3
+    same = oracle.keys_pairs(p, np.arange(300), np.arange(300), reverse=True)
+    assert np.all(same == oracle.keys_pairs(p, np.arange(300), np.arange(300)))
