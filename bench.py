@@ -355,7 +355,7 @@ def gpu_batch(args, rank, world, local, barrier):
         key = torch.empty((n, k), dtype=torch.float64, device=dev)
         outs.append((idx, key))
         arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, k, seeds[i], idx.data_ptr(), key.data_ptr())
-    prm = _lib.knnd_params(10000, 64, 1, 0, 0, 0, 0.0)
+    prm = _lib.knnd_params(10000, 64, 1, 0, 0, 0, 0.0, 0)
     b = ctypes.c_void_p()
     st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     _lib.check(lib.knnd_batch_create(ctypes.byref(b), count, ctypes.cast(arr, ctypes.c_void_p), _lib.KNND_F32,

@@ -83,6 +83,8 @@ typedef struct {
                                      of the previous round's graph (0); see knnd_round */
     float stop_delta;             /* > 0: also stop after a round with fewer than stop_delta * n * K
                                      updates, Dong et al.'s delta-proportion rule (Sec. 2, Table 1) (0) */
+    int32_t reverse;              /* comparator direction: 0 ranks y for x by D(x || y) (Sec. 2.2, the
+                                     paper's), 1 by D(y || x) (0); keys are then D(y || x) */
 } knnd_params;
 
 /* Why knnd_build stopped. */

@@ -47,7 +47,8 @@ KNND_NOALLOC_MAX_SAMPLES = 1 << 20
 class knnd_params(ctypes.Structure):
     _fields_ = [("fcc_samples", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("stop_on_zero_updates", ctypes.c_int32), ("debug", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("incremental", ctypes.c_int32), ("stop_delta", ctypes.c_float)]
+                ("timing", ctypes.c_int32), ("incremental", ctypes.c_int32), ("stop_delta", ctypes.c_float),
+                ("reverse", ctypes.c_int32)]
 
 
 class knnd_build_info(ctypes.Structure):

@@ -53,6 +53,10 @@ struct JoinArgs {
     // is 0 was in the previous round's pool and is not proposed again.
     const uint8_t *flag;
     const uint8_t *cof_new;
+    // reverse direction (key(x, y) = D(y || x) = negH(y) - <y, log x>): the launch
+    // swaps the coordinate and log tables, so rows read log x and columns read y;
+    // the offset negH then belongs to the column
+    int reverse;
 };
 
 // New-flag of the arc that makes row r (of hub v) a row of the tile: v -> x
@@ -86,7 +90,8 @@ struct MixedSmem {
     static __host__ __device__ int off_inc(int K) { return off_j(K) + ((32 * K + 15) & ~15); }
     static __host__ __device__ int off_rb(int K) { return off_inc(K) + 4 * 32; }
     static __host__ __device__ int off_cnew(int K) { return off_rb(K) + 8 * 32; }
-    static __host__ __device__ int warp_bytes(int K) { return off_cnew(K) + 64; }
+    static __host__ __device__ int off_hcol(int K) { return off_cnew(K) + 64; }
+    static __host__ __device__ int warp_bytes(int K) { return off_hcol(K) + 4 * 64; }
 };
 
 // Resident blocks of 128 threads per SM the kernel is compiled for: the
@@ -100,7 +105,7 @@ __host__ __device__ constexpr int mixed_min_blocks(int MP) {
 
 // INC: incremental proposals (a.flag non-NULL); compiled apart so that the
 // default form carries none of its state.
-template <int MP, bool INC>
+template <int MP, bool INC, bool REV>
 __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(JoinArgs a)
 {
     using S = MixedSmem<MP>;
@@ -117,6 +122,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
     int *sInc = reinterpret_cast<int *>(wbase + S::off_inc(K));
     int64_t *sRB = reinterpret_cast<int64_t *>(wbase + S::off_rb(K));
     unsigned char *sCnew = wbase + S::off_cnew(K);  // new-flags of the columns
+    float *sH = reinterpret_cast<float *>(wbase + S::off_hcol(K));  // reverse: RD(negH) of the columns
     const int64_t n = a.n;
     const int npairs = (K + 1) >> 1;
     const int G = 32 / npairs;                 // row groups
@@ -164,6 +170,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
             if (lane < K) {
                 sCid[lane] = rid0;
                 if (INC) sCnew[lane] = (unsigned char)rnew0;
+                if (REV) sH[lane] = rid0 >= 0 ? __double2float_rd(a.negH[rid0]) : 0.f;
             }
         } else {
             for (int j = lane; j < K; j += 32) {
@@ -174,8 +181,11 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 }
                 sCid[j] = id;
                 if (INC) sCnew[j] = (unsigned char)row_new(a, v, K, c0, j);
+                if (REV) sH[j] = id >= 0 ? __double2float_rd(a.negH[id]) : 0.f;
             }
         }
+        // reverse: the hub's own offset, for the co-friend pairs (y = v)
+        const float hv = REV ? __double2float_rd(a.negH[v]) : 0.f;
         __syncwarp();
         // no new column: only rows reached through a new arc can propose
         const bool any_col_new =
@@ -340,7 +350,8 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 for (int j = 0; j < K; ++j) {
                     const float d = drow[j];
                     const int cj = sCid[j];
-                    if (cj >= 0 && cj != rid && d >= ph && (!INC || rnew || sCnew[j])) {
+                    const float thr = REV ? __fsub_rd(sH[j], ph) : ph;
+                    if (cj >= 0 && cj != rid && d >= thr && (!INC || rnew || sCnew[j])) {
                         drow[q] = d;
                         jrow[q] = (unsigned char)j;
                         ++q;
@@ -363,7 +374,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                     acc = __fmaf_rn(xv.w, lw.w, acc);
                 }
                 cfd = acc;
-                cfpass = acc >= ph;
+                cfpass = acc >= (REV ? __fsub_rd(hv, ph) : ph);
             }
             const int count = q + (cfpass ? 1 : 0);
             int64_t rowbase = -1;
@@ -377,7 +388,9 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                         rowbase = -1;
                     }
                 }
-                if (cfpass && rowbase >= 0) a.bent[rowbase + q] = make_int2((int)sortable_bits(-cfd), (int)v);
+                if (cfpass && rowbase >= 0)
+                    a.bent[rowbase + q] =
+                        make_int2((int)sortable_bits(REV ? __fsub_rn(hv, cfd) : -cfd), (int)v);
             }
             // coalesced writes of the column survivors: entry k of the chunk's
             // flattened list goes to row t = the first with prefix > k
@@ -402,8 +415,12 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 const int t = lo;
                 const int qq = k - (t ? sInc[t - 1] : 0);
                 const int64_t rb = sRB[t];
-                if (rb >= 0)
-                    a.bent[rb + qq] = make_int2((int)sortable_bits(-sD[t * DS + qq]), sCid[sJ[t * K + qq]]);
+                if (rb >= 0) {
+                    const int j = sJ[t * K + qq];
+                    const float d = sD[t * DS + qq];
+                    // the entry orders the candidates like their keys: -d, or negH(y) - d
+                    a.bent[rb + qq] = make_int2((int)sortable_bits(REV ? __fsub_rn(sH[j], d) : -d), sCid[j]);
+                }
             }
             __syncwarp();
         }
@@ -436,6 +453,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
     for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
         int cid[CPL], cnew[CPL];
+        double cnh[CPL];  // reverse: the columns' negH (the offset of their keys)
         double Lc[CPL][MP];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -451,6 +469,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                 }
             }
             cid[c] = id;
+            cnh[c] = (a.reverse && id >= 0) ? a.negH[id] : 0.0;
             const double2 *lr = reinterpret_cast<const double2 *>(a.L64 + (int64_t)(id < 0 ? 0 : id) * MP);
 #pragma unroll
             for (int i2 = 0; i2 < MP / 2; ++i2) {
@@ -519,7 +538,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                 }
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
-                    const double k = rnh - acc[c];
+                    const double k = (a.reverse ? cnh[c] : rnh) - acc[c];
                     const bool pass = rrid >= 0 && cid[c] >= 0 && cid[c] != rrid && (rrnew || cnew[c]) &&
                                       lex_less(k, cid[c], rtk, rik);
                     const unsigned m = __ballot_sync(FULL, pass);
@@ -539,7 +558,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                     acc = __fma_rn(xv.x, lw.x, acc);
                     acc = __fma_rn(xv.y, lw.y, acc);
                 }
-                cfk = nh - acc;
+                cfk = (a.reverse ? a.negH[v] : nh) - acc;
                 cfpass = rnew && lex_less(cfk, (int)v, tk, ik);
             }
             int count = cfpass ? 1 : 0;
@@ -603,7 +622,8 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         using S = MixedSmem<MP>;
         const int threads = 128;
         const size_t smem = (size_t)S::warp_bytes(h->K) * (threads / 32);
-        auto kern = a.flag ? join_mixed_kernel<MP, true> : join_mixed_kernel<MP, false>;
+        auto kern = a.reverse ? (a.flag ? join_mixed_kernel<MP, true, true> : join_mixed_kernel<MP, false, true>)
+                              : (a.flag ? join_mixed_kernel<MP, true, false> : join_mixed_kernel<MP, false, false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -624,7 +644,8 @@ static cudaError_t run_join_cpl(knnd_handle *h, const JoinArgs &a)
 
 cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
 {
-    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K)) return launch_join_tc(h, idx);
+    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && !h->prm.reverse)
+        return launch_join_tc(h, idx);
     JoinArgs a;
     a.n = h->n;
     a.K = h->K;
@@ -647,6 +668,11 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
     a.iv = h->iv;
     a.flag = h->round_flag;
     a.cof_new = h->round_flag ? h->cof_new : nullptr;
+    a.reverse = h->prm.reverse;
+    if (a.reverse) {  // rows read log x, columns read y
+        std::swap(a.X32, a.L32);
+        std::swap(a.X64, a.L64);
+    }
     cudaMemsetAsync(h->bcnt, 0, sizeof(int32_t) * h->n, h->stream);
     h->launches += 1;
     switch (h->MP) {

@@ -162,7 +162,9 @@ struct knnd_handle {
     // precompute
     double *X64, *L64, *negH, *nx;
     float *X32, *L32;
-    unsigned long long *smax_bits;  // per instance: max |log y_i| as the bits of a non-negative double
+    // per instance i, bits of non-negative doubles: [3i] max |log y_j|, [3i+1] max |negH|,
+    // [3i+2] max sum_j |y_j| (the last two bound the reverse direction's FP32 errors)
+    unsigned long long *smax_bits;
     int32_t *err;                   // device error word
     // reverse CSR
     int32_t *deg;     // n: in-degree, then fill cursor

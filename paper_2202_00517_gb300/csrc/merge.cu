@@ -255,6 +255,14 @@ __device__ __forceinline__ double rescore(const MergeArgs &a, int64_t x, int y, 
     return nh - acc;
 }
 
+// key(x, y) in the handle's direction: forward negH(x) - <x, log y>; reverse
+// (y ranked by D(y || x)) the same chain with the roles swapped.  nh: negH(x).
+template <bool REV>
+__device__ __forceinline__ double rescore_dir(const MergeArgs &a, int64_t x, int y, double nh)
+{
+    return REV ? rescore(a, (int64_t)y, (int)x, a.negH[y]) : rescore(a, x, y, nh);
+}
+
 // ------------------------------------------------------------------ old-list set
 // Per-warp open-addressing set of the row's old friend indices in shared
 // memory (kHashSlots >= 2 K): about one probe per lookup.
@@ -311,7 +319,7 @@ struct Bounds {
 // Candidates are inserted one at a time.  Used for rows the fast path cannot
 // settle.  Mixed form: pass A keeps the K best upper bounds (threshold T),
 // pass B re-scores every candidate whose lower bound reaches T.
-template <int NE, bool MIXED>
+template <int NE, bool MIXED, bool REV>
 __device__ void serial_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &X, const int *tab, int64_t base,
                            int cnt, const Bounds<MIXED> &B, long long &rescored)
 {
@@ -358,7 +366,7 @@ __device__ void serial_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE>
         uint64_t k = 0;
         if (want) {
             if (MIXED) {
-                k = dkey(rescore(a, x, ci, B.nh));
+                k = dkey(rescore_dir<REV>(a, x, ci, B.nh));
                 rescored += 1;
             } else {
                 k = dkey(a.bkey[base + c0 + lane]);
@@ -504,7 +512,7 @@ __device__ __forceinline__ void insert_batch(WarpList<1> &X, int K, int lane, ui
     X.kth(K, xk, xi);
 }
 
-template <int NE, int R, bool MIXED>
+template <int NE, int R, bool MIXED, bool REV>
 __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &X, const int *tab, int2 *live_list,
                          int64_t base, int cnt, const Bounds<MIXED> &B, long long &rescored, BatchScratch &sb)
 {
@@ -575,7 +583,7 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
             const int2 e = live_list[c0 + lane];
             ci = e.x;
             if (MIXED) {
-                k = dkey(rescore(a, x, ci, B.nh));
+                k = dkey(rescore_dir<REV>(a, x, ci, B.nh));
                 rescored += 1;
             } else {
                 k = dkey(a.bkey[base + e.y]);
@@ -596,7 +604,8 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
     return true;
 }
 
-template <int NE, int R, bool MIXED>
+// REV: keys in the reverse direction (mixed forms re-score with the roles swapped).
+template <int NE, int R, bool MIXED, bool REV>
 __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
 {
     __shared__ int s_hash[8][kHashSlots];
@@ -618,10 +627,10 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
         survivors += cnt;
         if (cnt > 0) {
             Bounds<MIXED> B;
-            B.nh = MIXED ? a.negH[x] : 0.0;
+            B.nh = (MIXED && !REV) ? a.negH[x] : 0.0;
             B.E = MIXED ? a.Ex[x] : 0.0;
             hash_fill(tab, lane, K, X);
-            if (!fast_row<NE, R, MIXED>(a, x, lane, X, tab, live_list, base, cnt, B, rescored,
+            if (!fast_row<NE, R, MIXED, REV>(a, x, lane, X, tab, live_list, base, cnt, B, rescored,
                                         s_batch[NE == 1 ? (threadIdx.x >> 5) : 0])) {
                 // the row stays as it is here; merge_fallback_kernel finishes it
                 if (lane == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)x;
@@ -637,7 +646,7 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
 }
 
 // Rows the fast path could not settle, one warp each, on the serial path.
-template <int NE, bool MIXED>
+template <int NE, bool MIXED, bool REV>
 __global__ void __launch_bounds__(256) merge_fallback_kernel(MergeArgs a)
 {
     __shared__ int s_hash[8][kHashSlots];
@@ -655,10 +664,10 @@ __global__ void __launch_bounds__(256) merge_fallback_kernel(MergeArgs a)
         const int64_t base = (int64_t)K * K * x + (int64_t)(K + 1) * a.cof_off[x];
         const int cnt = bucket_count(a, x);
         Bounds<MIXED> B;
-        B.nh = MIXED ? a.negH[x] : 0.0;
+        B.nh = (MIXED && !REV) ? a.negH[x] : 0.0;
         B.E = MIXED ? a.Ex[x] : 0.0;
         hash_fill(tab, lane, K, X);
-        serial_row<NE, MIXED>(a, x, lane, X, tab, base, cnt, B, rescored);
+        serial_row<NE, MIXED, REV>(a, x, lane, X, tab, base, cnt, B, rescored);
         write_row(a, x, lane, X, newcount);
         long long nofb = 0;
         flush_row_counts(a, x, newcount, rescored, nofb);
@@ -694,21 +703,29 @@ cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *new
     cudaMemsetAsync(h->fb_count, 0, sizeof(int32_t), h->stream);
     const bool fp64 = h->prec == KNND_PREC_FP64;
     const unsigned fgrid = (unsigned)h->num_sms * 2;
+    // the FP64 form's keys come from the join (no re-score): one instance serves both directions
+    const bool rev = h->prm.reverse != 0;
     if (h->K <= 32) {
         if (fp64) {
-            merge_kernel<1, 4, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<1, false><<<fgrid, threads, 0, h->stream>>>(a);
+            merge_kernel<1, 4, false, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<1, false, false><<<fgrid, threads, 0, h->stream>>>(a);
+        } else if (!rev) {
+            merge_kernel<1, 4, true, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<1, true, false><<<fgrid, threads, 0, h->stream>>>(a);
         } else {
-            merge_kernel<1, 4, true><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<1, true><<<fgrid, threads, 0, h->stream>>>(a);
+            merge_kernel<1, 4, true, true><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<1, true, true><<<fgrid, threads, 0, h->stream>>>(a);
         }
     } else {
         if (fp64) {
-            merge_kernel<2, 8, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<2, false><<<fgrid, threads, 0, h->stream>>>(a);
+            merge_kernel<2, 8, false, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<2, false, false><<<fgrid, threads, 0, h->stream>>>(a);
+        } else if (!rev) {
+            merge_kernel<2, 8, true, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<2, true, false><<<fgrid, threads, 0, h->stream>>>(a);
         } else {
-            merge_kernel<2, 8, true><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<2, true><<<fgrid, threads, 0, h->stream>>>(a);
+            merge_kernel<2, 8, true, true><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+            merge_fallback_kernel<2, true, true><<<fgrid, threads, 0, h->stream>>>(a);
         }
     }
     h->launches += 2;

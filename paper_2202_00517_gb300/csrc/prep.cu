@@ -24,7 +24,7 @@ __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, const v
                                   unsigned long long *smax_bits, int32_t *err)
 {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double lmax = 0.0;
+    double lmax = 0.0, hmax = 0.0, nmax = 0.0;
     if (x < n) {
         double acc = 0.0, s = 0.0;
         bool bad = false;
@@ -55,22 +55,37 @@ __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, const v
         }
         negH[x] = acc;
         nx[x] = s;
+        hmax = fabs(acc);
+        nmax = s;
         if (bad) atomicOr(err, kErrDomain);
     }
-    if (iv.of) {  // several instances: one maximum each
-        if (x < n) atomicMax(&smax_bits[iv.of[x]], (unsigned long long)__double_as_longlong(lmax));
+    if (iv.of) {  // several instances: one set of maxima each
+        if (x < n) {
+            unsigned long long *mx = smax_bits + 3 * (int64_t)iv.of[x];
+            atomicMax(&mx[0], (unsigned long long)__double_as_longlong(lmax));
+            atomicMax(&mx[1], (unsigned long long)__double_as_longlong(hmax));
+            atomicMax(&mx[2], (unsigned long long)__double_as_longlong(nmax));
+        }
         return;
     }
-    // block max of |L| -> one atomicMax on the (monotone) bits of a non-negative double
-    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    __shared__ double wmax[32];
+    // block maxima -> one atomicMax each on the (monotone) bits of non-negative doubles
+    for (int o = 16; o > 0; o >>= 1) {
+        lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        hmax = fmax(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+        nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    }
+    __shared__ double wmax[3][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) wmax[w] = lmax;
+    if (lane == 0) {
+        wmax[0][w] = lmax;
+        wmax[1][w] = hmax;
+        wmax[2][w] = nmax;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 3) {
         double b = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b = fmax(b, wmax[i]);
-        atomicMax(smax_bits, (unsigned long long)__double_as_longlong(b));
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b = fmax(b, wmax[threadIdx.x][i]);
+        atomicMax(&smax_bits[threadIdx.x], (unsigned long long)__double_as_longlong(b));
     }
 }
 
@@ -84,7 +99,7 @@ cudaError_t launch_precompute_from(knnd_handle *h, const void *points, int64_t l
 {
     const int threads = 256;
     const int64_t blocks = (h->n + threads - 1) / threads;
-    cudaMemsetAsync(h->smax_bits, 0, sizeof(unsigned long long) * (h->ninst > 0 ? h->ninst : 1), h->stream);
+    cudaMemsetAsync(h->smax_bits, 0, sizeof(unsigned long long) * 3 * (h->ninst > 0 ? h->ninst : 1), h->stream);
     if (h->dtype == KNND_F32)
         precompute_kernel<float><<<(unsigned)blocks, threads, 0, h->stream>>>(
             (const float *)points, ld, ptrs, lds, h->iv, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32,
@@ -119,9 +134,10 @@ __device__ __forceinline__ double key_fp64(const double *__restrict__ X64, const
 // drawn from Philox stream (seed, x, 0, kTagInit): y' uniform in [0, n-1),
 // y = y' + (y' >= x), a repeat drawn again.  Rows sorted by (key, idx).
 // ---------------------------------------------------------------------------
+// reverse: y is ranked for x by D(y || x) = key(y, x).
 __global__ void init_graph_kernel(int64_t n, int K, int MP, const double *__restrict__ X64,
                                   const double *__restrict__ L64, const double *__restrict__ negH, uint64_t seed,
-                                  InstView iv, int32_t *__restrict__ idx, double *__restrict__ key,
+                                  InstView iv, int reverse, int32_t *__restrict__ idx, double *__restrict__ key,
                                   uint8_t *__restrict__ flag)
 {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,7 +163,8 @@ __global__ void init_graph_kernel(int64_t n, int K, int MP, const double *__rest
         if (dup) continue;
         ids[cnt++] = y;
     }
-    for (int t = 0; t < K; ++t) ks[t] = key_fp64(X64, L64, negH, MP, x, ids[t]);
+    for (int t = 0; t < K; ++t)
+        ks[t] = reverse ? key_fp64(X64, L64, negH, MP, ids[t], x) : key_fp64(X64, L64, negH, MP, x, ids[t]);
     for (int t = 1; t < K; ++t) {  // insertion sort by (key, idx)
         double kk = ks[t];
         int ii = ids[t];
@@ -172,7 +189,7 @@ cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, doubl
     const int threads = 128;
     const int64_t blocks = (h->n + threads - 1) / threads;
     init_graph_kernel<<<(unsigned)blocks, threads, 0, h->stream>>>(h->n, h->K, h->MP, h->X64, h->L64, h->negH,
-                                                                   seed, h->iv, idx, key, newflag);
+                                                                   seed, h->iv, h->prm.reverse, idx, key, newflag);
     h->launches += 1;
     return cudaGetLastError();
 }

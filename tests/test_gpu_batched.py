@@ -95,3 +95,18 @@ def test_batched_delta_stop_equals_separate_builds():
         assert b["updates"] == ref["updates"] and torch.equal(b["idx"], ref["idx"]), i
         reasons.add(b["stop_reason"])
     assert knnd.api._lib.KNND_STOP_DELTA in reasons
+
+
+def test_batched_reverse_direction_equals_separate_builds():
+    import paper_2202_00517_gb300 as knnd
+    shapes = _mix(16, 12)
+    pts = [torch.from_numpy(dirichlet_points(n, m, 700 + i, np.float32)).cuda() for i, (n, m, K) in enumerate(shapes)]
+    Ks = [K for _, _, K in shapes]
+    seeds = [0x5EED0200 + i for i in range(len(shapes))]
+    res = knnd.build_batched(pts, Ks, seeds, fcc_samples=700, reverse=True)
+    for i, (n, m, K) in enumerate(shapes):
+        h = knnd.Handle(n, m, K, dtype="f32", fcc_samples=700, reverse=True)
+        ref = h.build(pts[i], seeds[i])
+        h.close()
+        assert res[i]["rounds"] == ref["rounds"] and res[i]["updates"] == ref["updates"], i
+        assert torch.equal(res[i]["idx"], ref["idx"]) and torch.equal(res[i]["key"], ref["key"]), i

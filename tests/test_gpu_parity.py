@@ -37,15 +37,15 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000, incremental=True):
+def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000, incremental=True, reverse=False):
     n, m = pts.shape
     p = _dev(pts)
-    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, fcc_samples=S, incremental=incremental)
+    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, fcc_samples=S, incremental=incremental, reverse=reverse)
     pts64 = pts.astype(np.float64)
     gi, gk, _ = h.init_graph(p, seed)
-    ri, rk = oracle.init_graph(pts64, K, seed)
+    ri, rk = oracle.init_graph(pts64, K, seed, reverse=reverse)
     assert np.array_equal(gi.cpu().numpy(), ri)
-    compare_graphs(pts64, gi.cpu().numpy(), gk.cpu().numpy(), ri, rk, max_tie_rows=0)
+    compare_graphs(pts64, gi.cpu().numpy(), gk.cpu().numpy(), ri, rk, max_tie_rows=0, reverse=reverse)
     upd = torch.zeros(1, dtype=torch.int64, device="cuda")
     hits = torch.zeros(1, dtype=torch.int64, device="cuda")
     total_ties = 0
@@ -56,8 +56,8 @@ def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000, incremental
         flag = _dev(rf)
         h.round(None, seed, r, idx, key, flag, upd, hits)
         h.sync()
-        ni, nk, nf, nu, _ = oracle.round_(pts64, ri)
-        ties = compare_graphs(pts64, idx.cpu().numpy(), key.cpu().numpy(), ni, nk)
+        ni, nk, nf, nu, _ = oracle.round_(pts64, ri, reverse=reverse)
+        ties = compare_graphs(pts64, idx.cpu().numpy(), key.cpu().numpy(), ni, nk, reverse=reverse)
         total_ties += ties
         if ties == 0:
             assert np.array_equal(idx.cpu().numpy(), ni)
@@ -247,3 +247,29 @@ def test_delta_proportion_stop_matches_oracle(knnd, prec):
     assert out["stop_reason"] == knnd.api._lib.KNND_STOP_DELTA
     assert out["updates"] == list(ref["updates"]) and out["fcc_hits"] == list(ref["hits"])
     assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,m,K,dtype", [(2000, 6, 10, "f64"), (1500, 21, 20, "f32"), (800, 65, 32, "f32")])
+def test_reverse_direction_lockstep(knnd, prec, n, m, K, dtype):
+    # the variant comparator: x ranks y by D(y||x); every round against the oracle's
+    pts = dirichlet_points(n, m, 23, np.float32 if dtype == "f32" else np.float64)
+    assert _lockstep(knnd, pts, K, 23, prec, rounds=3, dtype=dtype, S=500, reverse=True) <= max(2, n // 500)
+
+
+def test_reverse_direction_build(knnd):
+    # free-running: the three forms give the same graph, and the oracle's
+    n, m, K, seed, S = 3000, 11, 12, 29, 2000
+    pts = dirichlet_points(n, m, seed, np.float64)
+    ref = oracle.build(pts, K, seed, S=S, reverse=True)
+    outs = {}
+    for prec in PRECS:
+        h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, reverse=True)
+        outs[prec] = h.build(_dev(pts), seed)
+        h.close()
+    for prec, out in outs.items():
+        assert out["rounds"] == ref["rounds"] and out["updates"] == list(ref["updates"]), prec
+        assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"]), prec
+        assert torch.equal(out["key"], outs["fp64"]["key"]), prec
+    fwd = oracle.build(pts, K, seed, S=S)
+    assert not np.array_equal(fwd["idx"], ref["idx"])  # the two directions rank differently
