@@ -157,27 +157,49 @@ void orc_logs(const double *pts, int64_t n, int m, double *L, double *negH)
     }
 }
 
-/* Direction of the comparator.  0 (the paper's, Sec. 2.2, Sec. 4.4): x ranks
- * y by D(x||y) = key(x, y).  1 (a variant: the divergence is asymmetric, and
- * the comparator is any function of x, Sec. 2 item (a)): x ranks y by
- * D(y||x) = key(y, x).  Set before the calls that key pairs. */
-static int orc_dir = 0;
+/* The comparator of x (Sec. 2 item (a): any function of x that ranks the
+ * other points; set before the calls that key pairs):
+ *   0  D(x||y) = key(x, y), the paper's (Sec. 2.2, Sec. 4.4);
+ *   1  D(y||x) = key(y, x), the KL divergence the other way round;
+ *   2  |x - y|^2 = (|x|^2 - 2 <x, y>) + |y|^2, a symmetric metric comparator,
+ *      |x|^2 and <x, y> sequential fma chains from 0 (2 <x, y> is exact). */
+static int orc_cmp = 0;
 
-void orc_set_direction(int32_t reverse) { orc_dir = reverse ? 1 : 0; }
+void orc_set_comparator(int32_t c) { orc_cmp = (c == 1 || c == 2) ? c : 0; }
 
-/* key(x, y) = negH(x) - sum_i x_i * log(y_i), the inner sum an fma chain
- * from 0 over i = 0..m-1; in the reverse direction the two roles swap. */
-static double orc_key_from_tables(const double *pts, const double *L, const double *negH,
+/* Per-point tables of the comparator: KL forms L = log(x), off = negH(x);
+ * squared Euclidean L unused, off = |x|^2. */
+static void orc_tables(const double *pts, int64_t n, int m, double *L, double *off)
+{
+    if (orc_cmp != 2) {
+        orc_logs(pts, n, m, L, off);
+        return;
+    }
+    for (int64_t y = 0; y < n; ++y) {
+        double acc = 0.0;
+        for (int i = 0; i < m; ++i) acc = fma(pts[y * m + i], pts[y * m + i], acc);
+        off[y] = acc;
+    }
+}
+
+/* key(x, y) for the comparator: KL negH(x) - sum_i x_i * log(y_i) (the inner
+ * sum an fma chain from 0 over i = 0..m-1), the roles swapped for 1;
+ * squared Euclidean (off(x) - 2 sum_i x_i y_i) + off(y). */
+static double orc_key_from_tables(const double *pts, const double *L, const double *off,
                                   int m, int64_t x, int64_t y)
 {
-    if (orc_dir) {
+    double dot = 0.0;
+    if (orc_cmp == 2) {
+        for (int i = 0; i < m; ++i) dot = fma(pts[x * m + i], pts[y * m + i], dot);
+        return (off[x] - 2.0 * dot) + off[y];
+    }
+    if (orc_cmp == 1) {
         const int64_t t = x;
         x = y;
         y = t;
     }
-    double dot = 0.0;
     for (int i = 0; i < m; ++i) dot = fma(pts[x * m + i], L[y * m + i], dot);
-    return negH[x] - dot;
+    return off[x] - dot;
 }
 
 /* Keys for a list of (x, y) pairs, building its own log table. */
@@ -186,7 +208,7 @@ void orc_keys_pairs(const double *pts, int64_t n, int m, const int32_t *xs, cons
 {
     double *L = (double *)malloc(sizeof(double) * (size_t)n * (size_t)m);
     double *negH = (double *)malloc(sizeof(double) * (size_t)n);
-    orc_logs(pts, n, m, L, negH);
+    orc_tables(pts, n, m, L, negH);
     for (int64_t p = 0; p < npairs; ++p) out[p] = orc_key_from_tables(pts, L, negH, m, xs[p], ys[p]);
     free(L);
     free(negH);
@@ -227,7 +249,7 @@ void orc_init_graph(const double *pts, int64_t n, int m, int K, uint64_t seed,
 {
     double *L = (double *)malloc(sizeof(double) * (size_t)n * (size_t)m);
     double *negH = (double *)malloc(sizeof(double) * (size_t)n);
-    orc_logs(pts, n, m, L, negH);
+    orc_tables(pts, n, m, L, negH);
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t x = 0; x < n; ++x) {
         orc_stream s;
@@ -357,7 +379,7 @@ int64_t orc_round(const double *pts, int64_t n, int m, int K, const int32_t *idx
 {
     double *L = (double *)malloc(sizeof(double) * (size_t)n * (size_t)m);
     double *negH = (double *)malloc(sizeof(double) * (size_t)n);
-    orc_logs(pts, n, m, L, negH);
+    orc_tables(pts, n, m, L, negH);
     orc_cofriends cf;
     orc_cofriends_build(idx_in, n, K, &cf);
     int64_t maxdeg = 0;
@@ -480,7 +502,7 @@ void orc_bruteforce(const double *pts, int64_t n, int m, int K, const int32_t *q
 {
     double *L = (double *)malloc(sizeof(double) * (size_t)n * (size_t)m);
     double *negH = (double *)malloc(sizeof(double) * (size_t)n);
-    orc_logs(pts, n, m, L, negH);
+    orc_tables(pts, n, m, L, negH);
 #pragma omp parallel
     {
         orc_cand *c = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)n);

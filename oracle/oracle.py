@@ -66,7 +66,7 @@ def _load():
             "orc_pools": (None, [P, i64, ctypes.c_int, i64, i64, P, P]),
             "orc_indegree": (None, [P, i64, ctypes.c_int, P]),
             "orc_fcc": (i64, [P, i64, ctypes.c_int, u64, i32, i32]),
-            "orc_set_direction": (None, [i32]),
+            "orc_set_comparator": (None, [i32]),
             "orc_build": (i32, [P, i64, ctypes.c_int, ctypes.c_int, u64, i32, i32, i32, ctypes.c_double,
                                 P, P, P, P, P]),
             "orc_bruteforce": (None, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P]),
@@ -85,19 +85,22 @@ def _load():
 _dir_lock = threading.Lock()
 
 
-class _direction:
-    """Comparator direction for the calls inside: reverse=True ranks y for x by
-    D(y||x) instead of D(x||y)."""
+COMPARATORS = {"kl": 0, "kl_reverse": 1, "sqeuclidean": 2}
 
-    def __init__(self, reverse: bool):
-        self.reverse = bool(reverse)
+
+class _comparator:
+    """Comparator for the calls inside: "kl" ranks y for x by D(x||y) (the
+    paper's), "kl_reverse" by D(y||x), "sqeuclidean" by |x - y|^2."""
+
+    def __init__(self, comparator):
+        self.c = COMPARATORS[comparator]
 
     def __enter__(self):
         _dir_lock.acquire()
-        _load().orc_set_direction(int(self.reverse))
+        _load().orc_set_comparator(self.c)
 
     def __exit__(self, *exc):
-        _load().orc_set_direction(0)
+        _load().orc_set_comparator(0)
         _dir_lock.release()
 
 
@@ -150,31 +153,32 @@ def logs(points):
     return L, negH
 
 
-def keys_pairs(points, xs, ys, reverse: bool = False) -> np.ndarray:
-    """Canonical FP64 key(x, y) = negH(x) - <x, log y> for each pair (reverse:
-    key(y, x), the rank of y for x by D(y||x))."""
+def keys_pairs(points, xs, ys, comparator: str = "kl") -> np.ndarray:
+    """Canonical FP64 key of each pair under the comparator: "kl" negH(x) - <x, log y>,
+    "kl_reverse" the same with the roles swapped (D(y||x)), "sqeuclidean"
+    (|x|^2 - 2 <x, y>) + |y|^2."""
     p = _pts(points)
     n, m = p.shape
     xs = np.ascontiguousarray(xs, dtype=np.int32)
     ys = np.ascontiguousarray(ys, dtype=np.int32)
     out = np.zeros(len(xs))
-    with _direction(reverse):
+    with _comparator(comparator):
         _load().orc_keys_pairs(_p(p), n, m, _p(xs), _p(ys), len(xs), _p(out))
     return out
 
 
-def init_graph(points, K: int, seed: int, reverse: bool = False):
+def init_graph(points, K: int, seed: int, comparator: str = "kl"):
     """Initial random K-out graph (idx n x K int32, key n x K float64), rows sorted."""
     p = _pts(points)
     n, m = p.shape
     idx = np.zeros((n, K), dtype=np.int32)
     key = np.zeros((n, K))
-    with _direction(reverse):
+    with _comparator(comparator):
         _load().orc_init_graph(_p(p), n, m, K, seed, _p(idx), _p(key))
     return idx, key
 
 
-def round_(points, idx_in, x0: int = 0, x1: int | None = None, reverse: bool = False):
+def round_(points, idx_in, x0: int = 0, x1: int | None = None, comparator: str = "kl"):
     """One synchronous round from graph idx_in.  Rows [x0, x1) are computed.
 
     Returns (idx, key, newflag, updates, proposals); rows outside [x0, x1) of
@@ -189,7 +193,7 @@ def round_(points, idx_in, x0: int = 0, x1: int | None = None, reverse: bool = F
     key = np.zeros((n, K))
     flag = np.zeros((n, K), dtype=np.uint8)
     props = np.zeros(1, dtype=np.int64)
-    with _direction(reverse):
+    with _comparator(comparator):
         upd = _load().orc_round(_p(p), n, m, K, _p(g), x0, x1, _p(idx), _p(key), _p(flag), _p(props))
     return idx, key, flag, int(upd), int(props[0])
 
@@ -224,7 +228,7 @@ def fcc(idx, seed: int, round_no: int, S: int) -> int:
 
 
 def build(points, K: int, seed: int, S: int = 10000, max_rounds: int = 64, stop_on_zero: bool = True,
-          stop_delta: float = 0.0, reverse: bool = False):
+          stop_delta: float = 0.0, comparator: str = "kl"):
     """Full build: returns dict(idx, key, rounds, updates[rounds], hits[rounds+1], proposals).
     stop_delta > 0: also stop after a round with fewer than stop_delta*n*K updates."""
     p = _pts(points)
@@ -234,21 +238,21 @@ def build(points, K: int, seed: int, S: int = 10000, max_rounds: int = 64, stop_
     upd = np.zeros(max_rounds, dtype=np.int64)
     hits = np.zeros(max_rounds + 1, dtype=np.int64)
     props = np.zeros(1, dtype=np.int64)
-    with _direction(reverse):
+    with _comparator(comparator):
         r = _load().orc_build(_p(p), n, m, K, seed, S, max_rounds, int(stop_on_zero), float(stop_delta), _p(idx),
                               _p(key), _p(upd), _p(hits), _p(props))
     return {"idx": idx, "key": key, "rounds": int(r), "updates": upd[:r].copy(),
             "hits": hits[:r + 1].copy(), "proposals": int(props[0])}
 
 
-def bruteforce(points, K: int, queries=None, reverse: bool = False):
+def bruteforce(points, K: int, queries=None, comparator: str = "kl"):
     """Exact K-NN lists (by (key, idx)) of the query points."""
     p = _pts(points)
     n, m = p.shape
     q = np.arange(n, dtype=np.int32) if queries is None else np.ascontiguousarray(queries, dtype=np.int32)
     idx = np.zeros((len(q), K), dtype=np.int32)
     key = np.zeros((len(q), K))
-    with _direction(reverse):
+    with _comparator(comparator):
         _load().orc_bruteforce(_p(p), n, m, K, _p(q), len(q), _p(idx), _p(key))
     return idx, key
 

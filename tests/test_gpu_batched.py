@@ -103,9 +103,9 @@ def test_batched_reverse_direction_equals_separate_builds():
     pts = [torch.from_numpy(dirichlet_points(n, m, 700 + i, np.float32)).cuda() for i, (n, m, K) in enumerate(shapes)]
     Ks = [K for _, _, K in shapes]
     seeds = [0x5EED0200 + i for i in range(len(shapes))]
-    res = knnd.build_batched(pts, Ks, seeds, fcc_samples=700, reverse=True)
+    res = knnd.build_batched(pts, Ks, seeds, fcc_samples=700, comparator="kl_reverse")
     for i, (n, m, K) in enumerate(shapes):
-        h = knnd.Handle(n, m, K, dtype="f32", fcc_samples=700, reverse=True)
+        h = knnd.Handle(n, m, K, dtype="f32", fcc_samples=700, comparator="kl_reverse")
         ref = h.build(pts[i], seeds[i])
         h.close()
         assert res[i]["rounds"] == ref["rounds"] and res[i]["updates"] == ref["updates"], i

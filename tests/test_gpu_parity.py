@@ -37,15 +37,16 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000, incremental=True, reverse=False):
+def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000, incremental=True, comparator="kl"):
     n, m = pts.shape
     p = _dev(pts)
-    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, fcc_samples=S, incremental=incremental, reverse=reverse)
+    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, fcc_samples=S, incremental=incremental,
+                    comparator=comparator)
     pts64 = pts.astype(np.float64)
     gi, gk, _ = h.init_graph(p, seed)
-    ri, rk = oracle.init_graph(pts64, K, seed, reverse=reverse)
+    ri, rk = oracle.init_graph(pts64, K, seed, comparator=comparator)
     assert np.array_equal(gi.cpu().numpy(), ri)
-    compare_graphs(pts64, gi.cpu().numpy(), gk.cpu().numpy(), ri, rk, max_tie_rows=0, reverse=reverse)
+    compare_graphs(pts64, gi.cpu().numpy(), gk.cpu().numpy(), ri, rk, max_tie_rows=0, comparator=comparator)
     upd = torch.zeros(1, dtype=torch.int64, device="cuda")
     hits = torch.zeros(1, dtype=torch.int64, device="cuda")
     total_ties = 0
@@ -56,8 +57,8 @@ def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000, incremental
         flag = _dev(rf)
         h.round(None, seed, r, idx, key, flag, upd, hits)
         h.sync()
-        ni, nk, nf, nu, _ = oracle.round_(pts64, ri, reverse=reverse)
-        ties = compare_graphs(pts64, idx.cpu().numpy(), key.cpu().numpy(), ni, nk, reverse=reverse)
+        ni, nk, nf, nu, _ = oracle.round_(pts64, ri, comparator=comparator)
+        ties = compare_graphs(pts64, idx.cpu().numpy(), key.cpu().numpy(), ni, nk, comparator=comparator)
         total_ties += ties
         if ties == 0:
             assert np.array_equal(idx.cpu().numpy(), ni)
@@ -254,17 +255,17 @@ def test_delta_proportion_stop_matches_oracle(knnd, prec):
 def test_reverse_direction_lockstep(knnd, prec, n, m, K, dtype):
     # the variant comparator: x ranks y by D(y||x); every round against the oracle's
     pts = dirichlet_points(n, m, 23, np.float32 if dtype == "f32" else np.float64)
-    assert _lockstep(knnd, pts, K, 23, prec, rounds=3, dtype=dtype, S=500, reverse=True) <= max(2, n // 500)
+    assert _lockstep(knnd, pts, K, 23, prec, rounds=3, dtype=dtype, S=500, comparator="kl_reverse") <= max(2, n // 500)
 
 
 def test_reverse_direction_build(knnd):
     # free-running: the three forms give the same graph, and the oracle's
     n, m, K, seed, S = 3000, 11, 12, 29, 2000
     pts = dirichlet_points(n, m, seed, np.float64)
-    ref = oracle.build(pts, K, seed, S=S, reverse=True)
+    ref = oracle.build(pts, K, seed, S=S, comparator="kl_reverse")
     outs = {}
     for prec in PRECS:
-        h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, reverse=True)
+        h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="kl_reverse")
         outs[prec] = h.build(_dev(pts), seed)
         h.close()
     for prec, out in outs.items():

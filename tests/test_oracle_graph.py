@@ -10,15 +10,18 @@ import networkx as nx
 import numpy as np
 import pytest
 from scipy import stats
+from scipy.spatial.distance import cdist
 from scipy.special import rel_entr
 
 import oracle
 from paper_2202_00517_gb300.datagen import dirichlet_points
 
 
-def _scipy_keys(p, x, ys, reverse=False):
-    if reverse:  # y ranked for x by D(y||x)
+def _scipy_keys(p, x, ys, comparator="kl"):
+    if comparator == "kl_reverse":  # y ranked for x by D(y||x)
         return rel_entr(p[ys], p[x][None, :]).sum(1)
+    if comparator == "sqeuclidean":
+        return cdist(p[x][None, :], p[ys], "sqeuclidean")[0]
     return rel_entr(p[x][None, :], p[ys]).sum(1)
 
 
@@ -79,19 +82,21 @@ def _python_pool(idx, x):
     return pool
 
 
-@pytest.mark.parametrize("reverse", [False, True])
-def test_round_equals_independent_pool_topk(reverse):
+@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean"])
+def test_round_equals_independent_pool_topk(comparator):
     n, m, K = 80, 4, 5
     p = dirichlet_points(n, m, 21, np.float64)
-    idx0, _ = oracle.init_graph(p, K, 21, reverse=reverse)
+    if comparator == "sqeuclidean":  # any finite coordinates
+        p = np.random.default_rng(21).standard_normal((n, m))
+    idx0, _ = oracle.init_graph(p, K, 21, comparator=comparator)
     pools = oracle.pools(idx0)
-    idx1, key1, flag, upd, props = oracle.round_(p, idx0, reverse=reverse)
+    idx1, key1, flag, upd, props = oracle.round_(p, idx0, comparator=comparator)
     _check_rows(idx1, key1, n, K)
     newcount = 0
     for x in range(n):
         pool = sorted(_python_pool(idx0, x))
         assert np.array_equal(pools[x], np.array(pool)), x
-        keys = _scipy_keys(p, x, np.array(pool), reverse)
+        keys = _scipy_keys(p, x, np.array(pool), comparator)
         order = np.lexsort((np.array(pool), keys))
         best = np.array(pool)[order[:K]]
         kb = keys[order[:K + 1]]
@@ -154,14 +159,16 @@ def test_round_row_range():
 
 
 # ---------------------------------------------------------------- brute force
-@pytest.mark.parametrize("reverse", [False, True])
-def test_bruteforce_matches_full_matrix(reverse):
+@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean"])
+def test_bruteforce_matches_full_matrix(comparator):
     n, m, K = 300, 6, 9
     p = dirichlet_points(n, m, 13, np.float64)
-    bi, bk = oracle.bruteforce(p, K, reverse=reverse)
+    bi, bk = oracle.bruteforce(p, K, comparator=comparator)
     D = rel_entr(p[:, None, :], p[None, :, :]).sum(-1)  # D[x, y] = D(x||y)
-    if reverse:
+    if comparator == "kl_reverse":
         D = D.T.copy()  # row x: D(y||x)
+    elif comparator == "sqeuclidean":
+        D = cdist(p, p, "sqeuclidean")
     np.fill_diagonal(D, np.inf)
     for x in range(n):
         order = np.lexsort((np.arange(n), D[x]))[:K]

@@ -95,11 +95,25 @@ def test_reverse_direction_matches_scipy():
     rng = np.random.default_rng(1)
     xs = rng.integers(0, 300, 3000)
     ys = rng.integers(0, 300, 3000)
-    k = oracle.keys_pairs(p, xs, ys, reverse=True)
+    k = oracle.keys_pairs(p, xs, ys, comparator="kl_reverse")
     ref = rel_entr(p[ys], p[xs]).sum(axis=1)
     scale = np.abs((p[ys] * np.log(p[ys])).sum(1)) + (p[ys] * np.abs(np.log(p[xs]))).sum(1)
     assert np.all(np.abs(k - ref) <= 1e-13 * scale)
     # the two directions differ (the divergence is not symmetric) but agree on x = y
     assert np.max(np.abs(k - oracle.keys_pairs(p, xs, ys))) > 1e-3
-    same = oracle.keys_pairs(p, np.arange(300), np.arange(300), reverse=True)
+    same = oracle.keys_pairs(p, np.arange(300), np.arange(300), comparator="kl_reverse")
     assert np.all(same == oracle.keys_pairs(p, np.arange(300), np.arange(300)))
+
+
+def test_squared_euclidean_matches_numpy():
+    # the metric comparator: (|x|^2 - 2<x, y>) + |y|^2, for any finite coordinates
+    p = np.random.default_rng(2).standard_normal((300, 13)) * 3.0
+    rng = np.random.default_rng(3)
+    xs = rng.integers(0, 300, 3000)
+    ys = rng.integers(0, 300, 3000)
+    k = oracle.keys_pairs(p, xs, ys, comparator="sqeuclidean")
+    ref = ((p[xs] - p[ys]) ** 2).sum(1)
+    scale = (p[xs] ** 2).sum(1) + (p[ys] ** 2).sum(1)
+    assert np.all(np.abs(k - ref) <= 1e-14 * scale)
+    # symmetric, up to the last rounding of the two orders of the sum
+    assert np.allclose(k, oracle.keys_pairs(p, ys, xs, comparator="sqeuclidean"), rtol=0, atol=1e-14 * scale.max())
