@@ -83,9 +83,15 @@ typedef struct {
                                      of the previous round's graph (0); see knnd_round */
     float stop_delta;             /* > 0: also stop after a round with fewer than stop_delta * n * K
                                      updates, Dong et al.'s delta-proportion rule (Sec. 2, Table 1) (0) */
-    int32_t reverse;              /* comparator direction: 0 ranks y for x by D(x || y) (Sec. 2.2, the
-                                     paper's), 1 by D(y || x) (0); keys are then D(y || x) */
+    int32_t comparator;           /* KNND_CMP_*: how x ranks the other points (KNND_CMP_KL) */
 } knnd_params;
+
+/* Comparators (Sec. 2 item (a): the comparator of x is any function of x that
+ * ranks the other points; keys returned are the comparator's values). */
+#define KNND_CMP_KL 0          /* D(x || y), the paper's (Sec. 2.2, Sec. 4.4); coordinates > 0 */
+#define KNND_CMP_KL_REVERSE 1  /* D(y || x): the asymmetric divergence the other way round; coordinates > 0 */
+#define KNND_CMP_SQEUCLIDEAN 2 /* |x - y|^2 = (|x|^2 - 2 <x, y>) + |y|^2 (fma chains): a symmetric metric
+                                  comparator; any finite coordinates */
 
 /* Why knnd_build stopped. */
 #define KNND_STOP_FCC 1        /* clustering hits did not increase (Sec. 3.3 (iv)) */

@@ -33,6 +33,9 @@ KNND_STOP_FCC = 1
 KNND_STOP_ZERO = 2
 KNND_STOP_MAX_ROUNDS = 3
 KNND_STOP_DELTA = 4
+KNND_CMP_KL = 0
+KNND_CMP_KL_REVERSE = 1
+KNND_CMP_SQEUCLIDEAN = 2
 
 EXPORTS = [
     "knnd_create", "knnd_destroy", "knnd_set_stream", "knnd_prepare", "knnd_init_graph", "knnd_round",
@@ -48,7 +51,7 @@ class knnd_params(ctypes.Structure):
     _fields_ = [("fcc_samples", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("stop_on_zero_updates", ctypes.c_int32), ("debug", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("incremental", ctypes.c_int32), ("stop_delta", ctypes.c_float),
-                ("reverse", ctypes.c_int32)]
+                ("comparator", ctypes.c_int32)]
 
 
 class knnd_build_info(ctypes.Structure):

@@ -17,6 +17,7 @@ from ._lib import check
 _PREC = {"fp64": _lib.KNND_PREC_FP64, "mixed": _lib.KNND_PREC_MIXED_FP32,
          "mixed_fp32": _lib.KNND_PREC_MIXED_FP32, "bf16x3": _lib.KNND_PREC_MIXED_BF16X3,
          "auto": _lib.KNND_PREC_AUTO}
+_CMP = {"kl": _lib.KNND_CMP_KL, "kl_reverse": _lib.KNND_CMP_KL_REVERSE, "sqeuclidean": _lib.KNND_CMP_SQEUCLIDEAN}
 _DTYPE = {"f32": _lib.KNND_F32, "f64": _lib.KNND_F64, torch.float32: _lib.KNND_F32,
           torch.float64: _lib.KNND_F64}
 
@@ -47,14 +48,14 @@ class Handle:
 
     def __init__(self, n: int, m: int, K: int, dtype="f32", precision="mixed", fcc_samples: int = 10000,
                  max_rounds: int = 64, stop_on_zero_updates: bool = True, debug: bool = False,
-                 timing: bool = False, incremental: bool = False, stop_delta: float = 0.0, reverse: bool = False,
+                 timing: bool = False, incremental: bool = False, stop_delta: float = 0.0, comparator: str = "kl",
                  stream=None):
         lib = _lib.load()
         self.n, self.m, self.K = n, m, K
         self.dtype = _DTYPE[dtype]
         self.torch_dtype = torch.float32 if self.dtype == _lib.KNND_F32 else torch.float64
         prm = _lib.knnd_params(fcc_samples, max_rounds, int(stop_on_zero_updates), int(debug), int(timing),
-                               int(incremental), float(stop_delta), int(reverse))
+                               int(incremental), float(stop_delta), _CMP[comparator])
         h = ctypes.c_void_p()
         check(lib.knnd_create(ctypes.byref(h), n, m, K, self.dtype, _PREC[precision], ctypes.byref(prm),
                               _stream_ptr(stream)), "knnd_create")
@@ -163,7 +164,7 @@ def build(points, K: int, seed: int = 0, precision: str = "mixed", **kw) -> dict
 
 def build_batched(points_list, Ks, seeds, precision: str = "mixed", fcc_samples: int = 10000,
                   max_rounds: int = 64, stop_on_zero_updates: bool = True, workspace_limit: int = 0,
-                  incremental: bool = False, stop_delta: float = 0.0, reverse: bool = False, stream=None,
+                  incremental: bool = False, stop_delta: float = 0.0, comparator: str = "kl", stream=None,
                   outputs=None):
     """Batched form: build many independent instances together.
 
@@ -187,7 +188,7 @@ def build_batched(points_list, Ks, seeds, precision: str = "mixed", fcc_samples:
         outs.append((idx, key))
         arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, K, sd, idx.data_ptr(), key.data_ptr())
     prm = _lib.knnd_params(fcc_samples, max_rounds, int(stop_on_zero_updates), 0, 0, int(incremental),
-                           float(stop_delta), int(reverse))
+                           float(stop_delta), _CMP[comparator])
     infos = (_lib.knnd_build_info * count)()
     check(lib.knnd_build_batched(count, ctypes.cast(arr, ctypes.c_void_p), dtype, _PREC[precision],
                                  ctypes.byref(prm), workspace_limit, ctypes.cast(infos, ctypes.c_void_p),

@@ -162,7 +162,7 @@ knnd_params default_params()
     p.timing = 0;
     p.incremental = 0;
     p.stop_delta = 0.f;
-    p.reverse = 0;
+    p.comparator = KNND_CMP_KL;
     return p;
 }
 
@@ -175,8 +175,8 @@ void configure(knnd_handle *h, int64_t n, int32_t m, int32_t K)
     // c_m of |fp32 dot - fp64 dot| <= c_m sum_i |x_i log y_i|: m FP32 fma roundings,
     // the FP32 rounding of log y_i and of x_i, doubled-rounding slack; 1% headroom.
     h->bound_c = (double)(m + 6) * 0x1p-24 * 1.01;
-    // (the reverse direction runs the FP32 join in every mixed form)
-    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, K) && !h->prm.reverse)
+    // (the other comparators run the FP32 join in every mixed form)
+    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, K) && h->prm.comparator == KNND_CMP_KL)
         h->bound_c = bound_c_bf16x3(h->MP);
     h->bucket_cap = n * K * (2 * (int64_t)K + 1);
     h->prepared = false;
@@ -312,7 +312,7 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
     if (prm.incremental != 0 && prm.incremental != 1) return KNND_EINVAL;
     if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
-    if (prm.reverse != 0 && prm.reverse != 1) return KNND_EINVAL;
+    if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_SQEUCLIDEAN) return KNND_EINVAL;
     // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
     if ((int64_t)K * K + (int64_t)(K + 1) * (n - 1) >= ((int64_t)1 << 31)) return KNND_EOVERFLOW;
     knnd::Caps caps;

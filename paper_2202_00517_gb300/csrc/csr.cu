@@ -11,7 +11,7 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
                                  int32_t *__restrict__ deg, double *__restrict__ tau, int32_t *__restrict__ idxK,
                                  const double *__restrict__ negH, const double *__restrict__ nx,
                                  const unsigned long long *__restrict__ smax_bits, InstView iv, double bound_c,
-                                 int reverse,
+                                 int cmp,
                                  RowMeta *__restrict__ meta, double *__restrict__ Ex, int32_t *err)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -27,7 +27,7 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
         const double t = key[e];
         tau[x] = t;
         idxK[x] = v;
-        if (meta && !reverse) {
+        if (meta && cmp == KNND_CMP_KL) {
             // |fp32 dot - fp64 dot| <= c_m * sum_i |x_i||log y_i| <= c_m * nx(x) * max|log|.
             // margin covers the FP64 roundings of the key and threshold arithmetic.
             const double smax = __longlong_as_double((long long)smax_bits[3 * iv.at(x)]);
@@ -37,22 +37,26 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
             Ex[x] = E;
             meta[x].phi = __double2float_rd(nh - t - E);
         } else if (meta) {
-            // reverse direction, key(x, y) = negH(y) - <y, log x>: the tile's dot d~
-            // of y's coordinates with x's logs is off by at most
-            // E1 = c_m * max_y sum|y_i| * max|log| (+ underflow).  The join rejects y
-            // when d~ < RD(RD(negH(y)) - phi) with phi = RU(tau + E1 + margin) >= tau + E1,
-            // which proves negH(y) - d > tau.  The candidate's FP32 entry is
-            // u = RN(RD(negH(y)) - d~); |u - key| <= E1 + 2^-22 (max|negH| + max sum|y| max|log| + 1)
-            // covers the roundings of RD(negH), of the subtraction and of |u|, and the
-            // merge bounds keys by u +- Ex (no per-row offset).
+            // comparators with a column offset, key(x, y) = ro(x) - s <R(x), C(y)> + co(y):
+            // reverse KL (ro = 0, co = negH(y), s = 1, R = log x, C = y) and squared
+            // Euclidean (ro = |x|^2, co = |y|^2, s = 2, R = x, C = y).  The tile's FP32
+            // dot d~ is off by at most c_m * sum_i |R_i||C_i| (+ underflow) <=
+            // E1 = c_m * max sum_j |y_j| * max |table entry|, per instance.  The join rejects
+            // y when d~ < RD(RD(co(y)/s) - phi) with phi = RU((tau - ro)/s + E1 + margin),
+            // which proves key > tau.  The candidate's entry is u = s RN(RD(co(y)/s) - d~),
+            // and |ro + u - key| <= s E1 + 2^-22 (max|co| + s max sum|y| max|C| + 1) + margin
+            // covers the roundings of co/s, of the subtraction and of u: the merge bounds
+            // keys by ro + u +- Ex.
             const unsigned long long *mx = smax_bits + 3 * (int64_t)iv.at(x);
             const double smax = __longlong_as_double((long long)mx[0]);
             const double hmax = __longlong_as_double((long long)mx[1]);
             const double nmax = __longlong_as_double((long long)mx[2]);
+            const double sc = cmp == KNND_CMP_SQEUCLIDEAN ? 2.0 : 1.0;
+            const double ro = cmp == KNND_CMP_SQEUCLIDEAN ? negH[x] : 0.0;
             const double E1 = bound_c * nmax * smax + 0x1p-100;
-            const double margin = 0x1p-40 * (fabs(t) + hmax + nmax * smax + 1.0);
-            Ex[x] = E1 + 0x1p-22 * (hmax + nmax * smax + 1.0) + margin;
-            meta[x].phi = __double2float_ru(t + E1 + margin);
+            const double margin = 0x1p-40 * (fabs(t) + fabs(ro) + hmax + sc * nmax * smax + 1.0);
+            Ex[x] = sc * E1 + 0x1p-22 * (hmax + sc * nmax * smax + 1.0) + margin;
+            meta[x].phi = __double2float_ru((t - ro) / sc + E1 + margin);
         }
     }
 }
@@ -164,7 +168,7 @@ cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double 
     cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
     const bool mixed = h->prec != KNND_PREC_FP64;
     csr_count_kernel<<<eblocks, threads, 0, h->stream>>>(idx, key, n, K, h->deg, h->tau, h->idxK, h->negH, h->nx,
-                                                         h->smax_bits, h->iv, h->bound_c, h->prm.reverse,
+                                                         h->smax_bits, h->iv, h->bound_c, h->prm.comparator,
                                                          mixed ? h->meta : nullptr,
                                                          h->Ex, h->err);
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;

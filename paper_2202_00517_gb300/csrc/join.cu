@@ -53,10 +53,14 @@ struct JoinArgs {
     // is 0 was in the previous round's pool and is not proposed again.
     const uint8_t *flag;
     const uint8_t *cof_new;
-    // reverse direction (key(x, y) = D(y || x) = negH(y) - <y, log x>): the launch
-    // swaps the coordinate and log tables, so rows read log x and columns read y;
-    // the offset negH then belongs to the column
-    int reverse;
+    // comparator (KNND_CMP_*).  Reverse KL (key(x, y) = negH(y) - <y, log x>): the
+    // launch swaps the coordinate and log tables, so rows read log x and columns
+    // read y, and the offset belongs to the column.  Squared Euclidean
+    // ((|x|^2 - 2 <x, y>) + |y|^2, negH holding the squared norms): both offsets,
+    // dot scale 2.  col_scale: 1 or 2; col_inv: its inverse (exact).
+    int cmp;
+    float col_scale;
+    double col_inv;
 };
 
 // New-flag of the arc that makes row r (of hub v) a row of the tile: v -> x
@@ -105,7 +109,9 @@ __host__ __device__ constexpr int mixed_min_blocks(int MP) {
 
 // INC: incremental proposals (a.flag non-NULL); compiled apart so that the
 // default form carries none of its state.
-template <int MP, bool INC, bool REV>
+// COL: the comparator has a column offset (reverse KL, squared Euclidean): the
+// filter threshold and the entry take RD(co(y)/s) of each column.
+template <int MP, bool INC, bool COL>
 __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(JoinArgs a)
 {
     using S = MixedSmem<MP>;
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
     int *sInc = reinterpret_cast<int *>(wbase + S::off_inc(K));
     int64_t *sRB = reinterpret_cast<int64_t *>(wbase + S::off_rb(K));
     unsigned char *sCnew = wbase + S::off_cnew(K);  // new-flags of the columns
-    float *sH = reinterpret_cast<float *>(wbase + S::off_hcol(K));  // reverse: RD(negH) of the columns
+    float *sH = reinterpret_cast<float *>(wbase + S::off_hcol(K));  // COL: RD(co(y) / s) of the columns
     const int64_t n = a.n;
     const int npairs = (K + 1) >> 1;
     const int G = 32 / npairs;                 // row groups
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
             if (lane < K) {
                 sCid[lane] = rid0;
                 if (INC) sCnew[lane] = (unsigned char)rnew0;
-                if (REV) sH[lane] = rid0 >= 0 ? __double2float_rd(a.negH[rid0]) : 0.f;
+                if (COL) sH[lane] = rid0 >= 0 ? __double2float_rd(a.negH[rid0] * a.col_inv) : 0.f;
             }
         } else {
             for (int j = lane; j < K; j += 32) {
@@ -181,11 +187,11 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 }
                 sCid[j] = id;
                 if (INC) sCnew[j] = (unsigned char)row_new(a, v, K, c0, j);
-                if (REV) sH[j] = id >= 0 ? __double2float_rd(a.negH[id]) : 0.f;
+                if (COL) sH[j] = id >= 0 ? __double2float_rd(a.negH[id] * a.col_inv) : 0.f;
             }
         }
-        // reverse: the hub's own offset, for the co-friend pairs (y = v)
-        const float hv = REV ? __double2float_rd(a.negH[v]) : 0.f;
+        // COL: the hub's own column value, for the co-friend pairs (y = v)
+        const float hv = COL ? __double2float_rd(a.negH[v] * a.col_inv) : 0.f;
         __syncwarp();
         // no new column: only rows reached through a new arc can propose
         const bool any_col_new =
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 for (int j = 0; j < K; ++j) {
                     const float d = drow[j];
                     const int cj = sCid[j];
-                    const float thr = REV ? __fsub_rd(sH[j], ph) : ph;
+                    const float thr = COL ? __fsub_rd(sH[j], ph) : ph;
                     if (cj >= 0 && cj != rid && d >= thr && (!INC || rnew || sCnew[j])) {
                         drow[q] = d;
                         jrow[q] = (unsigned char)j;
@@ -374,7 +380,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                     acc = __fmaf_rn(xv.w, lw.w, acc);
                 }
                 cfd = acc;
-                cfpass = acc >= (REV ? __fsub_rd(hv, ph) : ph);
+                cfpass = acc >= (COL ? __fsub_rd(hv, ph) : ph);
             }
             const int count = q + (cfpass ? 1 : 0);
             int64_t rowbase = -1;
@@ -390,7 +396,8 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 }
                 if (cfpass && rowbase >= 0)
                     a.bent[rowbase + q] =
-                        make_int2((int)sortable_bits(REV ? __fsub_rn(hv, cfd) : -cfd), (int)v);
+                        make_int2((int)sortable_bits(COL ? __fmul_rn(a.col_scale, __fsub_rn(hv, cfd)) : -cfd),
+                                  (int)v);
             }
             // coalesced writes of the column survivors: entry k of the chunk's
             // flattened list goes to row t = the first with prefix > k
@@ -418,8 +425,9 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 if (rb >= 0) {
                     const int j = sJ[t * K + qq];
                     const float d = sD[t * DS + qq];
-                    // the entry orders the candidates like their keys: -d, or negH(y) - d
-                    a.bent[rb + qq] = make_int2((int)sortable_bits(REV ? __fsub_rn(sH[j], d) : -d), sCid[j]);
+                    // the entry orders the candidates like their keys: -d, or s (co(y)/s - d)
+                    a.bent[rb + qq] = make_int2(
+                        (int)sortable_bits(COL ? __fmul_rn(a.col_scale, __fsub_rn(sH[j], d)) : -d), sCid[j]);
                 }
             }
             __syncwarp();
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
     for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
         int cid[CPL], cnew[CPL];
-        double cnh[CPL];  // reverse: the columns' negH (the offset of their keys)
+        double cnh[CPL];  // column offsets (reverse KL: negH(y); squared Euclidean: |y|^2)
         double Lc[CPL][MP];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -469,7 +477,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                 }
             }
             cid[c] = id;
-            cnh[c] = (a.reverse && id >= 0) ? a.negH[id] : 0.0;
+            cnh[c] = (a.cmp != KNND_CMP_KL && id >= 0) ? a.negH[id] : 0.0;
             const double2 *lr = reinterpret_cast<const double2 *>(a.L64 + (int64_t)(id < 0 ? 0 : id) * MP);
 #pragma unroll
             for (int i2 = 0; i2 < MP / 2; ++i2) {
@@ -538,7 +546,9 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                 }
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
-                    const double k = (a.reverse ? cnh[c] : rnh) - acc[c];
+                    const double k = a.cmp == KNND_CMP_KL           ? rnh - acc[c]
+                                     : a.cmp == KNND_CMP_KL_REVERSE ? cnh[c] - acc[c]
+                                                                    : (rnh - 2.0 * acc[c]) + cnh[c];
                     const bool pass = rrid >= 0 && cid[c] >= 0 && cid[c] != rrid && (rrnew || cnew[c]) &&
                                       lex_less(k, cid[c], rtk, rik);
                     const unsigned m = __ballot_sync(FULL, pass);
@@ -558,7 +568,9 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                     acc = __fma_rn(xv.x, lw.x, acc);
                     acc = __fma_rn(xv.y, lw.y, acc);
                 }
-                cfk = (a.reverse ? a.negH[v] : nh) - acc;
+                cfk = a.cmp == KNND_CMP_KL           ? nh - acc
+                      : a.cmp == KNND_CMP_KL_REVERSE ? a.negH[v] - acc
+                                                     : (nh - 2.0 * acc) + a.negH[v];
                 cfpass = rnew && lex_less(cfk, (int)v, tk, ik);
             }
             int count = cfpass ? 1 : 0;
@@ -622,8 +634,9 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         using S = MixedSmem<MP>;
         const int threads = 128;
         const size_t smem = (size_t)S::warp_bytes(h->K) * (threads / 32);
-        auto kern = a.reverse ? (a.flag ? join_mixed_kernel<MP, true, true> : join_mixed_kernel<MP, false, true>)
-                              : (a.flag ? join_mixed_kernel<MP, true, false> : join_mixed_kernel<MP, false, false>);
+        const bool col = a.cmp != KNND_CMP_KL;
+        auto kern = col ? (a.flag ? join_mixed_kernel<MP, true, true> : join_mixed_kernel<MP, false, true>)
+                        : (a.flag ? join_mixed_kernel<MP, true, false> : join_mixed_kernel<MP, false, false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -644,7 +657,7 @@ static cudaError_t run_join_cpl(knnd_handle *h, const JoinArgs &a)
 
 cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
 {
-    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && !h->prm.reverse)
+    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && h->prm.comparator == KNND_CMP_KL)
         return launch_join_tc(h, idx);
     JoinArgs a;
     a.n = h->n;
@@ -668,8 +681,10 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
     a.iv = h->iv;
     a.flag = h->round_flag;
     a.cof_new = h->round_flag ? h->cof_new : nullptr;
-    a.reverse = h->prm.reverse;
-    if (a.reverse) {  // rows read log x, columns read y
+    a.cmp = h->prm.comparator;
+    a.col_scale = a.cmp == KNND_CMP_SQEUCLIDEAN ? 2.f : 1.f;
+    a.col_inv = a.cmp == KNND_CMP_SQEUCLIDEAN ? 0.5 : 1.0;
+    if (a.cmp == KNND_CMP_KL_REVERSE) {  // rows read log x, columns read y
         std::swap(a.X32, a.L32);
         std::swap(a.X64, a.L64);
     }

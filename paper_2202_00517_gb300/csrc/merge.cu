@@ -255,12 +255,15 @@ __device__ __forceinline__ double rescore(const MergeArgs &a, int64_t x, int y, 
     return nh - acc;
 }
 
-// key(x, y) in the handle's direction: forward negH(x) - <x, log y>; reverse
-// (y ranked by D(y || x)) the same chain with the roles swapped.  nh: negH(x).
-template <bool REV>
+// key(x, y) under the comparator CMP: KL negH(x) - <x, log y>; reverse KL the
+// same chain with the roles swapped; squared Euclidean (|x|^2 - 2 <x, y>) + |y|^2
+// (the tables then hold the coordinates and the squared norms).  nh: negH(x).
+template <int CMP>
 __device__ __forceinline__ double rescore_dir(const MergeArgs &a, int64_t x, int y, double nh)
 {
-    return REV ? rescore(a, (int64_t)y, (int)x, a.negH[y]) : rescore(a, x, y, nh);
+    if (CMP == KNND_CMP_KL_REVERSE) return rescore(a, (int64_t)y, (int)x, a.negH[y]);
+    if (CMP == KNND_CMP_SQEUCLIDEAN) return (a.negH[x] + 2.0 * rescore(a, x, y, 0.0)) + a.negH[y];
+    return rescore(a, x, y, nh);
 }
 
 // ------------------------------------------------------------------ old-list set
@@ -319,7 +322,7 @@ struct Bounds {
 // Candidates are inserted one at a time.  Used for rows the fast path cannot
 // settle.  Mixed form: pass A keeps the K best upper bounds (threshold T),
 // pass B re-scores every candidate whose lower bound reaches T.
-template <int NE, bool MIXED, bool REV>
+template <int NE, bool MIXED, int CMP>
 __device__ void serial_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &X, const int *tab, int64_t base,
                            int cnt, const Bounds<MIXED> &B, long long &rescored)
 {
@@ -366,7 +369,7 @@ __device__ void serial_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE>
         uint64_t k = 0;
         if (want) {
             if (MIXED) {
-                k = dkey(rescore_dir<REV>(a, x, ci, B.nh));
+                k = dkey(rescore_dir<CMP>(a, x, ci, B.nh));
                 rescored += 1;
             } else {
                 k = dkey(a.bkey[base + c0 + lane]);
@@ -512,7 +515,7 @@ __device__ __forceinline__ void insert_batch(WarpList<1> &X, int K, int lane, ui
     X.kth(K, xk, xi);
 }
 
-template <int NE, int R, bool MIXED, bool REV>
+template <int NE, int R, bool MIXED, int CMP>
 __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &X, const int *tab, int2 *live_list,
                          int64_t base, int cnt, const Bounds<MIXED> &B, long long &rescored, BatchScratch &sb)
 {
@@ -583,7 +586,7 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
             const int2 e = live_list[c0 + lane];
             ci = e.x;
             if (MIXED) {
-                k = dkey(rescore_dir<REV>(a, x, ci, B.nh));
+                k = dkey(rescore_dir<CMP>(a, x, ci, B.nh));
                 rescored += 1;
             } else {
                 k = dkey(a.bkey[base + e.y]);
@@ -604,8 +607,10 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
     return true;
 }
 
-// REV: keys in the reverse direction (mixed forms re-score with the roles swapped).
-template <int NE, int R, bool MIXED, bool REV>
+// CMP: the comparator (KNND_CMP_*) the mixed forms re-score with; the entries'
+// u orders candidates like key - ro(x), ro = negH(x) for KL, |x|^2 for squared
+// Euclidean, 0 for reverse KL.
+template <int NE, int R, bool MIXED, int CMP>
 __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
 {
     __shared__ int s_hash[8][kHashSlots];
@@ -627,10 +632,10 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
         survivors += cnt;
         if (cnt > 0) {
             Bounds<MIXED> B;
-            B.nh = (MIXED && !REV) ? a.negH[x] : 0.0;
+            B.nh = (MIXED && CMP != KNND_CMP_KL_REVERSE) ? a.negH[x] : 0.0;
             B.E = MIXED ? a.Ex[x] : 0.0;
             hash_fill(tab, lane, K, X);
-            if (!fast_row<NE, R, MIXED, REV>(a, x, lane, X, tab, live_list, base, cnt, B, rescored,
+            if (!fast_row<NE, R, MIXED, CMP>(a, x, lane, X, tab, live_list, base, cnt, B, rescored,
                                         s_batch[NE == 1 ? (threadIdx.x >> 5) : 0])) {
                 // the row stays as it is here; merge_fallback_kernel finishes it
                 if (lane == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)x;
@@ -646,7 +651,7 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
 }
 
 // Rows the fast path could not settle, one warp each, on the serial path.
-template <int NE, bool MIXED, bool REV>
+template <int NE, bool MIXED, int CMP>
 __global__ void __launch_bounds__(256) merge_fallback_kernel(MergeArgs a)
 {
     __shared__ int s_hash[8][kHashSlots];
@@ -664,15 +669,22 @@ __global__ void __launch_bounds__(256) merge_fallback_kernel(MergeArgs a)
         const int64_t base = (int64_t)K * K * x + (int64_t)(K + 1) * a.cof_off[x];
         const int cnt = bucket_count(a, x);
         Bounds<MIXED> B;
-        B.nh = (MIXED && !REV) ? a.negH[x] : 0.0;
+        B.nh = (MIXED && CMP != KNND_CMP_KL_REVERSE) ? a.negH[x] : 0.0;
         B.E = MIXED ? a.Ex[x] : 0.0;
         hash_fill(tab, lane, K, X);
-        serial_row<NE, MIXED, REV>(a, x, lane, X, tab, base, cnt, B, rescored);
+        serial_row<NE, MIXED, CMP>(a, x, lane, X, tab, base, cnt, B, rescored);
         write_row(a, x, lane, X, newcount);
         long long nofb = 0;
         flush_row_counts(a, x, newcount, rescored, nofb);
     }
     flush_counts(a, newcount, rescored, 0);
+}
+
+template <int NE, int R, bool MIXED, int CMP>
+static void launch_merge_pair(knnd_handle *h, const MergeArgs &a, int64_t grid, unsigned fgrid, int threads)
+{
+    merge_kernel<NE, R, MIXED, CMP><<<(unsigned)grid, threads, 0, h->stream>>>(a);
+    merge_fallback_kernel<NE, MIXED, CMP><<<fgrid, threads, 0, h->stream>>>(a);
 }
 
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag)
@@ -703,30 +715,19 @@ cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *new
     cudaMemsetAsync(h->fb_count, 0, sizeof(int32_t), h->stream);
     const bool fp64 = h->prec == KNND_PREC_FP64;
     const unsigned fgrid = (unsigned)h->num_sms * 2;
-    // the FP64 form's keys come from the join (no re-score): one instance serves both directions
-    const bool rev = h->prm.reverse != 0;
+    // the FP64 form's keys come from the join (no re-score): one instance serves every comparator
     if (h->K <= 32) {
-        if (fp64) {
-            merge_kernel<1, 4, false, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<1, false, false><<<fgrid, threads, 0, h->stream>>>(a);
-        } else if (!rev) {
-            merge_kernel<1, 4, true, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<1, true, false><<<fgrid, threads, 0, h->stream>>>(a);
-        } else {
-            merge_kernel<1, 4, true, true><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<1, true, true><<<fgrid, threads, 0, h->stream>>>(a);
-        }
+        if (fp64) launch_merge_pair<1, 4, false, KNND_CMP_KL>(h, a, grid, fgrid, threads);
+        else if (h->prm.comparator == KNND_CMP_KL) launch_merge_pair<1, 4, true, KNND_CMP_KL>(h, a, grid, fgrid, threads);
+        else if (h->prm.comparator == KNND_CMP_KL_REVERSE)
+            launch_merge_pair<1, 4, true, KNND_CMP_KL_REVERSE>(h, a, grid, fgrid, threads);
+        else launch_merge_pair<1, 4, true, KNND_CMP_SQEUCLIDEAN>(h, a, grid, fgrid, threads);
     } else {
-        if (fp64) {
-            merge_kernel<2, 8, false, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<2, false, false><<<fgrid, threads, 0, h->stream>>>(a);
-        } else if (!rev) {
-            merge_kernel<2, 8, true, false><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<2, true, false><<<fgrid, threads, 0, h->stream>>>(a);
-        } else {
-            merge_kernel<2, 8, true, true><<<(unsigned)grid, threads, 0, h->stream>>>(a);
-            merge_fallback_kernel<2, true, true><<<fgrid, threads, 0, h->stream>>>(a);
-        }
+        if (fp64) launch_merge_pair<2, 8, false, KNND_CMP_KL>(h, a, grid, fgrid, threads);
+        else if (h->prm.comparator == KNND_CMP_KL) launch_merge_pair<2, 8, true, KNND_CMP_KL>(h, a, grid, fgrid, threads);
+        else if (h->prm.comparator == KNND_CMP_KL_REVERSE)
+            launch_merge_pair<2, 8, true, KNND_CMP_KL_REVERSE>(h, a, grid, fgrid, threads);
+        else launch_merge_pair<2, 8, true, KNND_CMP_SQEUCLIDEAN>(h, a, grid, fgrid, threads);
     }
     h->launches += 2;
     return cudaGetLastError();

@@ -16,9 +16,11 @@ namespace knnd {
 // ---------------------------------------------------------------------------
 // Points: pts + x * ld, or (several instances) the row x - base[i] of
 // instance i = iv.of[x] at ptrs[i] with row stride lds[i].
+// Squared Euclidean comparator (sqe): L is a copy of the coordinates and negH
+// holds |x|^2 (fma chain from 0); coordinates need only be finite.
 template <typename T>
 __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, const void *const *ptrs,
-                                  const int64_t *lds, InstView iv, int64_t n, int m, int MP,
+                                  const int64_t *lds, InstView iv, int sqe, int64_t n, int m, int MP,
                                   double *__restrict__ X64, double *__restrict__ L64, float *__restrict__ X32,
                                   float *__restrict__ L32, double *__restrict__ negH, double *__restrict__ nx,
                                   unsigned long long *smax_bits, int32_t *err)
@@ -39,11 +41,11 @@ __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, const v
             double v = 0.0, l = 0.0;
             if (i < m) {
                 v = (double)row[i];
-                if (!(v > 0.0) || !(v <= DBL_MAX)) {
+                if (sqe ? !(fabs(v) <= DBL_MAX) : (!(v > 0.0) || !(v <= DBL_MAX))) {
                     bad = true;
                     v = 1.0;  // keep the tables finite; the call reports EDOMAIN
                 }
-                l = log(v);
+                l = sqe ? v : log(v);
                 acc = __fma_rn(v, l, acc);
                 s += fabs(v);
                 lmax = fmax(lmax, fabs(l));
@@ -102,21 +104,22 @@ cudaError_t launch_precompute_from(knnd_handle *h, const void *points, int64_t l
     cudaMemsetAsync(h->smax_bits, 0, sizeof(unsigned long long) * 3 * (h->ninst > 0 ? h->ninst : 1), h->stream);
     if (h->dtype == KNND_F32)
         precompute_kernel<float><<<(unsigned)blocks, threads, 0, h->stream>>>(
-            (const float *)points, ld, ptrs, lds, h->iv, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32,
+            (const float *)points, ld, ptrs, lds, h->iv, h->prm.comparator == KNND_CMP_SQEUCLIDEAN, h->n, h->m, h->MP,
+            h->X64, h->L64, h->X32, h->L32,
             h->negH, h->nx, h->smax_bits, h->err);
     else
         precompute_kernel<double><<<(unsigned)blocks, threads, 0, h->stream>>>(
-            (const double *)points, ld, ptrs, lds, h->iv, h->n, h->m, h->MP, h->X64, h->L64, h->X32, h->L32,
+            (const double *)points, ld, ptrs, lds, h->iv, h->prm.comparator == KNND_CMP_SQEUCLIDEAN, h->n, h->m, h->MP,
+            h->X64, h->L64, h->X32, h->L32,
             h->negH, h->nx, h->smax_bits, h->err);
     h->launches += 1;
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Canonical FP64 key of (x, y): negH[x] - (fma chain over i of x_i * log y_i).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double key_fp64(const double *__restrict__ X64, const double *__restrict__ L64,
-                                           const double *__restrict__ negH, int MP, int64_t x, int64_t y)
+// fma chain over i of X64[x]_i * L64[y]_i, from 0 (padding terms are exact no-ops).
+__device__ __forceinline__ double dot_fp64(const double *__restrict__ X64, const double *__restrict__ L64, int MP,
+                                           int64_t x, int64_t y)
 {
     const double2 *xr = reinterpret_cast<const double2 *>(X64 + x * MP);
     const double2 *lr = reinterpret_cast<const double2 *>(L64 + y * MP);
@@ -126,7 +129,18 @@ __device__ __forceinline__ double key_fp64(const double *__restrict__ X64, const
         acc = __fma_rn(a.x, b.x, acc);
         acc = __fma_rn(a.y, b.y, acc);
     }
-    return negH[x] - acc;
+    return acc;
+}
+
+// The comparator's canonical FP64 key: KL negH(x) - <x, log y>; reverse KL the
+// same with the roles swapped; squared Euclidean (|x|^2 - 2 <x, y>) + |y|^2 (L64
+// then holds the coordinates and negH the squared norms).
+__device__ __forceinline__ double key_cmp(int cmp, const double *__restrict__ X64, const double *__restrict__ L64,
+                                          const double *__restrict__ negH, int MP, int64_t x, int64_t y)
+{
+    if (cmp == KNND_CMP_KL_REVERSE) return negH[y] - dot_fp64(X64, L64, MP, y, x);
+    if (cmp == KNND_CMP_SQEUCLIDEAN) return (negH[x] - 2.0 * dot_fp64(X64, L64, MP, x, y)) + negH[y];
+    return negH[x] - dot_fp64(X64, L64, MP, x, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -134,10 +148,10 @@ __device__ __forceinline__ double key_fp64(const double *__restrict__ X64, const
 // drawn from Philox stream (seed, x, 0, kTagInit): y' uniform in [0, n-1),
 // y = y' + (y' >= x), a repeat drawn again.  Rows sorted by (key, idx).
 // ---------------------------------------------------------------------------
-// reverse: y is ranked for x by D(y || x) = key(y, x).
+// cmp: the comparator (KNND_CMP_*), see key_cmp.
 __global__ void init_graph_kernel(int64_t n, int K, int MP, const double *__restrict__ X64,
                                   const double *__restrict__ L64, const double *__restrict__ negH, uint64_t seed,
-                                  InstView iv, int reverse, int32_t *__restrict__ idx, double *__restrict__ key,
+                                  InstView iv, int cmp, int32_t *__restrict__ idx, double *__restrict__ key,
                                   uint8_t *__restrict__ flag)
 {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -164,7 +178,7 @@ __global__ void init_graph_kernel(int64_t n, int K, int MP, const double *__rest
         ids[cnt++] = y;
     }
     for (int t = 0; t < K; ++t)
-        ks[t] = reverse ? key_fp64(X64, L64, negH, MP, ids[t], x) : key_fp64(X64, L64, negH, MP, x, ids[t]);
+        ks[t] = key_cmp(cmp, X64, L64, negH, MP, x, ids[t]);
     for (int t = 1; t < K; ++t) {  // insertion sort by (key, idx)
         double kk = ks[t];
         int ii = ids[t];
@@ -189,7 +203,7 @@ cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, doubl
     const int threads = 128;
     const int64_t blocks = (h->n + threads - 1) / threads;
     init_graph_kernel<<<(unsigned)blocks, threads, 0, h->stream>>>(h->n, h->K, h->MP, h->X64, h->L64, h->negH,
-                                                                   seed, h->iv, h->prm.reverse, idx, key, newflag);
+                                                                   seed, h->iv, h->prm.comparator, idx, key, newflag);
     h->launches += 1;
     return cudaGetLastError();
 }

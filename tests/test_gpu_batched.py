@@ -110,3 +110,19 @@ def test_batched_reverse_direction_equals_separate_builds():
         h.close()
         assert res[i]["rounds"] == ref["rounds"] and res[i]["updates"] == ref["updates"], i
         assert torch.equal(res[i]["idx"], ref["idx"]) and torch.equal(res[i]["key"], ref["key"]), i
+
+
+def test_batched_sqeuclidean_equals_separate_builds():
+    import paper_2202_00517_gb300 as knnd
+    shapes = _mix(16, 14)
+    rng = np.random.default_rng(8)
+    pts = [torch.from_numpy(rng.standard_normal((n, m)).astype(np.float32)).cuda() for n, m, K in shapes]
+    Ks = [K for _, _, K in shapes]
+    seeds = [0x5EED0300 + i for i in range(len(shapes))]
+    res = knnd.build_batched(pts, Ks, seeds, fcc_samples=700, comparator="sqeuclidean")
+    for i, (n, m, K) in enumerate(shapes):
+        h = knnd.Handle(n, m, K, dtype="f32", fcc_samples=700, comparator="sqeuclidean")
+        ref = h.build(pts[i], seeds[i])
+        h.close()
+        assert res[i]["rounds"] == ref["rounds"] and res[i]["updates"] == ref["updates"], i
+        assert torch.equal(res[i]["idx"], ref["idx"]) and torch.equal(res[i]["key"], ref["key"]), i

@@ -274,3 +274,56 @@ def test_reverse_direction_build(knnd):
         assert torch.equal(out["key"], outs["fp64"]["key"]), prec
     fwd = oracle.build(pts, K, seed, S=S)
     assert not np.array_equal(fwd["idx"], ref["idx"])  # the two directions rank differently
+
+
+def _gauss(n, m, seed, dtype=np.float64):
+    # any finite coordinates, both signs (the squared Euclidean comparator needs no simplex)
+    return (np.random.default_rng(seed).standard_normal((n, m)) * 2.0).astype(dtype)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,m,K,dtype,gauss", [(2000, 6, 10, "f64", True), (1500, 21, 20, "f32", True),
+                                                 (800, 65, 32, "f32", False), (1200, 128, 17, "f64", True)])
+def test_sqeuclidean_lockstep(knnd, prec, n, m, K, dtype, gauss):
+    npdt = np.float32 if dtype == "f32" else np.float64
+    pts = _gauss(n, m, 31, npdt) if gauss else dirichlet_points(n, m, 31, npdt)
+    assert _lockstep(knnd, pts, K, 31, prec, rounds=3, dtype=dtype, S=500, comparator="sqeuclidean") <= max(2, n // 500)
+
+
+def test_sqeuclidean_build(knnd):
+    n, m, K, seed, S = 3000, 9, 12, 37, 2000
+    pts = _gauss(n, m, seed)
+    ref = oracle.build(pts, K, seed, S=S, comparator="sqeuclidean")
+    outs = {}
+    for prec in PRECS:
+        h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="sqeuclidean")
+        outs[prec] = h.build(_dev(pts), seed)
+        h.close()
+    for prec, out in outs.items():
+        assert out["rounds"] == ref["rounds"] and out["updates"] == list(ref["updates"]), prec
+        assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"]), prec
+        assert torch.equal(out["key"], outs["fp64"]["key"]), prec
+    # recall against exact brute force: the metric comparator's neighbours are found
+    q = np.arange(0, n, 15).astype(np.int32)
+    bi, _ = oracle.bruteforce(pts, K, q, comparator="sqeuclidean")
+    got = outs["mixed"]["idx"].cpu().numpy()
+    rec = np.mean([len(set(bi[t]) & set(got[x])) / K for t, x in enumerate(q)])
+    assert rec > 0.9, rec
+
+
+def test_sqeuclidean_domain(knnd):
+    n, m, K = 300, 4, 6
+    pts = _gauss(n, m, 5)
+    h = knnd.Handle(n, m, K, dtype="f64", precision="mixed", comparator="sqeuclidean")
+    h.build(_dev(pts), 5)  # negative and zero coordinates are fine here
+    bad = pts.copy()
+    bad[7, 1] = np.nan
+    with pytest.raises(knnd.api._lib.KnndError) as e:
+        h.build(_dev(bad), 5)
+    assert e.value.status == knnd.api._lib.KNND_EDOMAIN
+    h.close()
+    hk = knnd.Handle(n, m, K, dtype="f64", precision="mixed")  # KL needs coordinates > 0
+    with pytest.raises(knnd.api._lib.KnndError) as e:
+        hk.build(_dev(pts), 5)
+    assert e.value.status == knnd.api._lib.KNND_EDOMAIN
+    hk.close()
