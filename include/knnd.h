@@ -1,6 +1,8 @@
 /*
  * knnd.h -- C ABI of the GB300 (sm_103a) K-nearest-neighbour descent library
- * for the Kullback-Leibler comparator on points of the probability simplex.
+ * for the Kullback-Leibler comparator on points of the probability simplex
+ * (and, as variants, the reverse KL divergence and the squared Euclidean
+ * distance: knnd_params.comparator).
  *
  * Method: Baron & Darling, "Empirical complexity of comparator-based nearest
  * neighbor descent", arXiv:2202.00517.
@@ -9,7 +11,7 @@
  *     each x to its K most similar objects;
  *   - comparator (Sec. 2.2, Sec. 4.4): y precedes z for x when
  *     D(x||y) < D(x||z), D(x||y) = sum_i x_i log(x_i / y_i); ties are broken
- *     by the smaller index;
+ *     by the smaller index (variants, Sec. 2 item (a): D(y||x), |x - y|^2);
  *   - initial graph (Sec. 3.2): every x picks K distinct friends uniformly;
  *   - one round (Sec. 3.1, Sec. 4.2): every x meets its co-friends, its
  *     friends' friends and its co-friends' friends; its new friend list is the
@@ -20,11 +22,14 @@
  * Conventions shared by every call:
  *   - Points: n rows of m coordinates, row-major with a leading dimension of
  *     `ld` elements (ld >= m), KNND_F32 or KNND_F64.  Every coordinate must be
- *     finite and > 0 (points need not sum to exactly 1; they are used as
- *     stored).  Point pointers are DEVICE pointers unless a name says _host.
+ *     finite and, for the KL comparators, > 0 (points need not sum to
+ *     exactly 1; they are used as stored).  Point pointers are DEVICE
+ *     pointers unless a name says _host.
  *   - Graph: idx is n x K int32 (row x = x's friends), key is n x K float64
  *     (key[x][t] = D(x || idx[x][t]) evaluated in FP64 as
- *     sum_i x_i log x_i - sum_i x_i log y_i), newflag is n x K uint8 (1 when
+ *     sum_i x_i log x_i - sum_i x_i log y_i, both sums fma chains from 0;
+ *     KNND_CMP_KL_REVERSE: D(idx[x][t] || x), the same with the roles
+ *     swapped; KNND_CMP_SQEUCLIDEAN: (|x|^2 - 2 <x, y>) + |y|^2), newflag is n x K uint8 (1 when
  *     the entry was not in the row before the call).  Each row is sorted by
  *     (key ascending, idx ascending).  Caller-owned device buffers.
  *   - Work is enqueued on the handle's stream (a cudaStream_t passed as
@@ -48,7 +53,7 @@ extern "C" {
 typedef int32_t knnd_status;
 #define KNND_OK 0
 #define KNND_EINVAL (-1)    /* bad argument: null pointer, shape or parameter out of range */
-#define KNND_EDOMAIN (-2)   /* a coordinate is not finite or not > 0 (found on the device) */
+#define KNND_EDOMAIN (-2)   /* a coordinate is not finite, or (KL comparators) not > 0 (found on the device) */
 #define KNND_ENOMEM (-3)    /* device allocation failed */
 #define KNND_ECUDA (-4)     /* a CUDA runtime call or kernel launch failed */
 #define KNND_ETIMEOUT (-5)  /* a bounded device wait ran out */
