@@ -82,7 +82,10 @@ typedef struct {
     int32_t fcc_samples;          /* S, samples of the clustering rate per round (10000) */
     int32_t max_rounds;           /* cap on rounds, 1..KNND_MAX_ROUNDS (64) */
     int32_t stop_on_zero_updates; /* also stop after a round with no update (1) */
-    int32_t debug;                /* 1: device bounds checks and error-bound audit (0) */
+    int32_t debug;                /* 1: device bounds checks and error-bound audit; 2: as 1, and the
+                                     tensor-core join's first tile of its first block issues no MMA,
+                                     so its bounded wait runs out: the call reports KNND_ETIMEOUT
+                                     (a test of the timeout path, with no fault) (0) */
     int32_t timing;               /* 1: CUDA events around every phase, see knnd_stats (0) */
     int32_t incremental;          /* 1: a round does not propose again a pair it met only through edges
                                      of the previous round's graph (0); see knnd_round */

@@ -313,6 +313,7 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     if (prm.incremental != 0 && prm.incremental != 1) return KNND_EINVAL;
     if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
     if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_SQEUCLIDEAN) return KNND_EINVAL;
+    if (prm.debug < 0 || prm.debug > 2) return KNND_EINVAL;
     // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
     if ((int64_t)K * K + (int64_t)(K + 1) * (n - 1) >= ((int64_t)1 << 31)) return KNND_EOVERFLOW;
     knnd::Caps caps;

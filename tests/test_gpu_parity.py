@@ -327,3 +327,23 @@ def test_sqeuclidean_domain(knnd):
         hk.build(_dev(pts), 5)
     assert e.value.status == knnd.api._lib.KNND_EDOMAIN
     hk.close()
+
+
+def test_bounded_wait_timeout_is_reported(knnd):
+    # debug = 2: the tensor-core join's first tile waits on a barrier that no MMA
+    # signals; the wait gives up after about a second, the call reports ETIMEOUT,
+    # and the GPU context stays usable (no fault is involved)
+    n, m, K, seed = 3000, 21, 20, 3
+    pts = _dev(dirichlet_points(n, m, seed, np.float32))
+    h = knnd.Handle(n, m, K, dtype="f32", precision="bf16x3", debug=2)
+    with pytest.raises(knnd.api._lib.KnndError) as e:
+        h.build(pts, seed)
+    assert e.value.status == knnd.api._lib.KNND_ETIMEOUT
+    h.close()
+    h = knnd.Handle(n, m, K, dtype="f32", precision="bf16x3")
+    out = h.build(pts, seed)
+    h.close()
+    ref = knnd.Handle(n, m, K, dtype="f32", precision="fp64")
+    r = ref.build(pts, seed)
+    ref.close()
+    assert torch.equal(out["idx"], r["idx"])
