@@ -144,11 +144,17 @@ def cpu_reference_step(pts64, g0i):
 
 
 def run_reference(args, rank, world):
+    """The oracle on the host cores, on the GPU arm's workload: a bounded sample per
+    step (round 1 for the first REF_ROWS rows; for the batched mix, whole builds of
+    evenly spaced instances).  Under torchrun only rank 0 runs and prints."""
     if rank != 0:
         return 0
     import oracle
-    pts64 = dirichlet_points(N, M, SEED, np.float32).astype(np.float64)
-    g0i, _ = oracle.init_graph(pts64, K, SEED)
+    if args.workload == "batch4096":
+        return run_reference_batch(args)
+    n, m, k, seed, desc = WORKLOADS[args.workload]
+    pts64 = dirichlet_points(n, m, seed, np.float32, threads=16).astype(np.float64)
+    g0i, _ = oracle.init_graph(pts64, k, seed)
     for _ in range(args.warmup):
         cpu_reference_step(pts64, g0i)
     ev, sec = 0, 0.0
@@ -158,17 +164,59 @@ def run_reference(args, rank, world):
         sec += s
     value = ev / sec
     cores = oracle.num_threads()
-    sample = (f"oracle round 1 (from its own initial graph) for rows [0, {REF_ROWS}) of the n=1e6 workload "
+    sample = (f"oracle round 1 (from its own initial graph) for rows [0, {REF_ROWS}) of the n={n} workload "
               "per step; setup (log table, co-friend lists over all n) included")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "m": M, "K": K, "seed": SEED,
+            "data": "synthetic", "config": {"workload": desc, "n": n, "m": m, "K": k, "seed": seed,
                                             "form": "CPU oracle, FP64", "parallelism": "cpu"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_reference_batch(args, per_step=4):
+    """Reference arm of the batched mix: per step, the oracle's whole builds of
+    `per_step` evenly spaced instances of the 4096 (their KL evaluations / time)."""
+    import oracle
+    from paper_2202_00517_gb300.datagen import instance_mix
+    mix = instance_mix(4096, 5)
+    picks = np.linspace(0, 4095, per_step * max(1, args.steps + args.warmup)).astype(int)
+    ev, sec, t = 0, 0.0, 0
+    for step in range(args.warmup + args.steps):
+        for i in picks[step * per_step:(step + 1) * per_step]:
+            n, m, k = mix[i]
+            p = dirichlet_points(n, m, 0x5EED0000 + int(i), np.float32).astype(np.float64)
+            t0 = time.perf_counter()
+            r = oracle.build(p, k, 0x5EED0000 + int(i), S=10000)
+            dt = time.perf_counter() - t0
+            if step >= args.warmup:
+                ev += evals_of(n, k, r["rounds"])
+                sec += dt
+                t += 1
+    value = ev / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "batched form: 4096 independent instances (sampled)",
+                                            "form": "CPU oracle, FP64", "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{t} evenly spaced instances of the 4096, whole builds"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def replica_max(values, device, world):
+    """Max over the ranks of each of `values`: the slowest replica sets the time."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -236,11 +284,7 @@ def gpu_single(args, name, rank, world, local, barrier):
         e2e_ev += evals_of(N, K, out["rounds"])
     h.close()
 
-    import torch.distributed as dist
-    t = torch.tensor([mixed["ms"], fp64["ms"] if fp64 else 0.0, e2e_sec], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    mixed_ms, fp64_ms, e2e_max = t.tolist()
+    mixed_ms, fp64_ms, e2e_max = replica_max([mixed["ms"], fp64["ms"] if fp64 else 0.0, e2e_sec], dev, world)
     if rank != 0:
         return None
     info = mixed["infos"][-1]
@@ -369,11 +413,17 @@ def gpu_batch(args, rank, world, local, barrier):
     barrier()
     clocks = Clocks(local)
     clocks.start()
-    t0 = time.perf_counter()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     for _ in range(args.steps):
         _lib.check(lib.knnd_batch_run(b, ctypes.cast(infos, ctypes.c_void_p)), "knnd_batch_run")
+    e1.record(stream)
+    e1.synchronize()
     torch.cuda.synchronize()
-    batched_s = (time.perf_counter() - t0) / args.steps
+    barrier()
+    batched_s = replica_max([e0.elapsed_time(e1) / 1e3 / args.steps], dev, world)[0]
     clk = clocks.stop()
     nsub, ws, l1 = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
     lib.knnd_batch_info(b, ctypes.byref(nsub), ctypes.byref(ws), ctypes.byref(l1))
