@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "knnd_internal.cuh"
 
 using namespace knnd;
@@ -25,6 +27,8 @@ knnd_status dalloc(knnd_handle *h, T **p, int64_t count)
 {
     *p = nullptr;
     if (count <= 0) return KNND_OK;
+    // a failing allocation, faked on the host for the tests of the clean-up path
+    if (h->fail_alloc_at > 0 && ++h->allocs == h->fail_alloc_at) return KNND_ENOMEM;
     const size_t bytes = sizeof(T) * (size_t)count;
     cudaError_t e = cudaMalloc((void **)p, bytes);
     if (e != cudaSuccess) {
@@ -81,8 +85,14 @@ void resolve_phases(knnd_handle *h)
     h->npend = 0;
 }
 
-int phase_begin(knnd_handle *h)
+// Phases are NVTX ranges (visible to a profiler's timeline; no cost without
+// one) and, with params.timing, CUDA-event intervals on the handle's stream.
+const char *const kPhaseName[KNND_NUM_PHASES] = {"knnd prepare", "knnd init", "knnd csr",
+                                                 "knnd join",    "knnd merge", "knnd fcc"};
+
+int phase_begin(knnd_handle *h, int phase)
 {
+    nvtxRangePushA(kPhaseName[phase]);
     if (!h->events_made) return -1;
     if (h->npend == knnd_handle::kMaxPending) resolve_phases(h);
     const int slot = h->npend;
@@ -92,6 +102,7 @@ int phase_begin(knnd_handle *h)
 
 void phase_end(knnd_handle *h, int slot, int phase)
 {
+    nvtxRangePop();
     if (slot < 0) return;
     cudaEventRecord(h->ev[2 * slot + 1], h->stream);
     h->pend_phase[slot] = phase;
@@ -109,7 +120,7 @@ knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
 {
     knnd_status s = check_points(h, points, ld);
     if (s) return s;
-    const int t = phase_begin(h);
+    const int t = phase_begin(h, KNND_PHASE_PREPARE);
     cudaError_t e = launch_precompute(h, points, ld);
     phase_end(h, t, KNND_PHASE_PREPARE);
     if (e != cudaSuccess) return cuda_status(e);
@@ -125,21 +136,21 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
     // incremental proposals read the flags of G_{r-1} (the join runs before the
     // merge overwrites them with those of G_r)
     h->round_flag = (h->prm.incremental && newflag) ? newflag : nullptr;
-    int t = phase_begin(h);
+    int t = phase_begin(h, KNND_PHASE_CSR);
     cudaError_t e = launch_reverse_csr(h, idx, key);
     phase_end(h, t, KNND_PHASE_CSR);
     if (e == cudaSuccess) {
-        t = phase_begin(h);
+        t = phase_begin(h, KNND_PHASE_JOIN);
         e = launch_join(h, idx);
         phase_end(h, t, KNND_PHASE_JOIN);
     }
     if (e == cudaSuccess) {
-        t = phase_begin(h);
+        t = phase_begin(h, KNND_PHASE_MERGE);
         e = launch_merge(h, idx, key, newflag);
         phase_end(h, t, KNND_PHASE_MERGE);
     }
     if (e == cudaSuccess && fcc_hits) {
-        t = phase_begin(h);
+        t = phase_begin(h, KNND_PHASE_FCC);
         e = launch_fcc(h, idx, seed, round, fcc_hits);
         phase_end(h, t, KNND_PHASE_FCC);
     }
@@ -198,6 +209,7 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
         delete h;
         return KNND_ECUDA;
     }
+    if (const char *f = std::getenv("KNND_TEST_FAIL_ALLOC")) h->fail_alloc_at = std::atoi(f);
     const int64_t n = c.n;
     knnd_status s = KNND_OK;
     const int64_t ntiles = (n + 2047) / 2048;
@@ -355,7 +367,7 @@ knnd_status knnd_init_graph(knnd_handle *h, const void *points, int64_t ld, uint
     } else if (!h->prepared) {
         return KNND_ESTATE;
     }
-    const int t = phase_begin(h);
+    const int t = phase_begin(h, KNND_PHASE_INIT);
     cudaError_t e = launch_init_graph(h, seed, idx, key, newflag);
     phase_end(h, t, KNND_PHASE_INIT);
     return cuda_status(e);
@@ -402,7 +414,7 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
     knnd_status s = do_prepare(h, points, ld);
     if (s) return s;
     if (!newflag && h->prm.incremental) newflag = h->flag_tmp;  // the rounds need the flags
-    int t = phase_begin(h);
+    int t = phase_begin(h, KNND_PHASE_INIT);
     cudaError_t e = launch_init_graph(h, seed, idx, key, newflag);
     phase_end(h, t, KNND_PHASE_INIT);
     if (e != cudaSuccess) return cuda_status(e);
@@ -410,7 +422,7 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
     int64_t *hst = h->cnt_host;
     e = cudaMemsetAsync(d, 0, sizeof(int64_t) * kCntNum, h->stream);
     if (e == cudaSuccess) {
-        t = phase_begin(h);
+        t = phase_begin(h, KNND_PHASE_FCC);
         e = launch_fcc(h, idx, seed, 0, d + kCntHits);
         phase_end(h, t, KNND_PHASE_FCC);
     }

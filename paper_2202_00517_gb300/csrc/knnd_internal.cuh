@@ -157,6 +157,8 @@ struct knnd_handle {
     cudaStream_t stream;
     int device;
     int num_sms;
+    int fail_alloc_at;  // > 0: the fail_alloc_at-th workspace allocation fails (KNND_TEST_FAIL_ALLOC)
+    int allocs;
     bool prepared;
 
     // precompute
