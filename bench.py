@@ -23,6 +23,7 @@ import os
 import re
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -65,7 +66,9 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        # the samples go to a scratch file (KNND_CLOCKS_DIR keeps them, e.g. next to a run's logs)
+        d = os.environ.get("KNND_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"knnd_clocks_gpu{index}_{os.getpid()}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
