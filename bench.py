@@ -236,8 +236,11 @@ def gpu_single(args, name, rank, world, local, barrier):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
-    def run_form(prec, steps, warmup, clocks=None, incremental=False):
-        h = knnd.Handle(N, M, K, dtype="f32", precision=prec, timing=True, incremental=incremental)
+    def run_form(prec, steps, warmup, clocks=None, incremental=False, loop="host"):
+        # host loop: per-phase CUDA events (the join's launch time for the roofline);
+        # graph loop: one graph launch per build, no events inside it
+        h = knnd.Handle(N, M, K, dtype="f32", precision=prec, timing=loop == "host", incremental=incremental,
+                        loop=loop)
         idx, key, flag = h.new_graph(dev)
         for _ in range(warmup):
             h.build(pts, SEED, idx, key, flag)
@@ -270,6 +273,8 @@ def gpu_single(args, name, rank, world, local, barrier):
     fp64 = run_form("fp64", args.fp64_steps, 1) if args.fp64_steps > 0 else None
     # the same build with incremental proposals (same graph, fewer candidates), one step
     incr = run_form(args.form, 1, 1, incremental=True) if args.steps > 0 else None
+    # the same build with the round loop on the device (CUDA graph with a while node)
+    gloop = run_form(args.form, min(args.steps, 5), 1, loop="graph") if args.steps > 0 else None
 
     # end to end through the public API from pinned host memory (H2D points, D2H idx+key)
     h = knnd.Handle(N, M, K, dtype="f32", precision=args.form)
@@ -356,6 +361,13 @@ def gpu_single(args, name, rank, world, local, barrier):
         line["incremental_proposals"]["same_graph"] = bool(
             a_info["rounds"] == info["rounds"] and a_info["updates"] == info["updates"]
             and torch.equal(a_info["idx"], info["idx"]) and torch.equal(a_info["key"], info["key"]))
+    if gloop:
+        g_info = gloop["infos"][-1]
+        line["round_loop"] = {
+            "host_build_s": mixed_ms / steps / 1e3, "graph_build_s": gloop["ms"] / len(gloop["infos"]) / 1e3,
+            "graph_launches_per_build": gloop["stats"]["kernel_launches"] / len(gloop["infos"]),
+            "same_graph": bool(g_info["rounds"] == info["rounds"] and g_info["updates"] == info["updates"]
+                               and torch.equal(g_info["idx"], info["idx"]) and torch.equal(g_info["key"], info["key"]))}
     if fp64:
         line["build_s_fp64"] = fp64_ms / max(1, args.fp64_steps) / 1e3
         line["evals_per_s_fp64"] = world * fp64["evals"] / (fp64_ms / 1e3)

@@ -92,7 +92,18 @@ typedef struct {
     float stop_delta;             /* > 0: also stop after a round with fewer than stop_delta * n * K
                                      updates, Dong et al.'s delta-proportion rule (Sec. 2, Table 1) (0) */
     int32_t comparator;           /* KNND_CMP_*: how x ranks the other points (KNND_CMP_KL) */
+    int32_t loop;                 /* KNND_LOOP_*: how knnd_build runs its rounds (KNND_LOOP_AUTO) */
 } knnd_params;
+
+/* The round loop of knnd_build.  Both give the same graph and report. */
+#define KNND_LOOP_AUTO 0  /* GRAPH, or HOST when timing = 1 */
+#define KNND_LOOP_HOST 1  /* the host launches every round and reads the stop decision after it
+                             (one stream synchronisation per round) */
+#define KNND_LOOP_GRAPH 2 /* one CUDA-graph launch per build: a while node whose body is one round
+                             and a one-thread kernel that applies the stop rule on the device and
+                             sets the node's condition; one synchronisation per build.  The graph
+                             is captured on the first build and kept for later builds with the same
+                             idx, key and newflag pointers.  Not with timing = 1 (EINVAL) */
 
 /* Comparators (Sec. 2 item (a): the comparator of x is any function of x that
  * ranks the other points; keys returned are the comparator's values). */
@@ -203,11 +214,13 @@ knnd_status knnd_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t 
 
 /* Full build (Sec. 3): initial graph, then rounds until the clustering hits
  * of round r do not exceed those of round r-1, or (stop_on_zero_updates) a
- * round makes no update, or max_rounds.  points: device (non-NULL).
- * idx, key: out, device n x K (G after the stopping round).  newflag:
- * device n x K or NULL.  info: host, filled.  Synchronises the stream once
- * per round to read the stop decision.
- * Errors: EINVAL, EDOMAIN, ECUDA, EOVERFLOW. */
+ * round makes no update, or (stop_delta) too few updates, or max_rounds.
+ * points: device (non-NULL).  idx, key: out, device n x K (G after the
+ * stopping round).  newflag: device n x K or NULL.  info: host, filled.
+ * Synchronises the stream once per round (KNND_LOOP_HOST) or once per build
+ * (KNND_LOOP_GRAPH; the first build with new idx/key/newflag pointers also
+ * captures and instantiates the round graph, which the handle then keeps).
+ * Errors: EINVAL, EDOMAIN, ECUDA, EOVERFLOW, ENOMEM (loop state). */
 knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t seed, int32_t *idx,
                        double *key, uint8_t *newflag, knnd_build_info *info);
 

@@ -36,6 +36,9 @@ KNND_STOP_DELTA = 4
 KNND_CMP_KL = 0
 KNND_CMP_KL_REVERSE = 1
 KNND_CMP_SQEUCLIDEAN = 2
+KNND_LOOP_AUTO = 0
+KNND_LOOP_HOST = 1
+KNND_LOOP_GRAPH = 2
 
 EXPORTS = [
     "knnd_create", "knnd_destroy", "knnd_set_stream", "knnd_prepare", "knnd_init_graph", "knnd_round",
@@ -51,7 +54,7 @@ class knnd_params(ctypes.Structure):
     _fields_ = [("fcc_samples", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("stop_on_zero_updates", ctypes.c_int32), ("debug", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("incremental", ctypes.c_int32), ("stop_delta", ctypes.c_float),
-                ("comparator", ctypes.c_int32)]
+                ("comparator", ctypes.c_int32), ("loop", ctypes.c_int32)]
 
 
 class knnd_build_info(ctypes.Structure):

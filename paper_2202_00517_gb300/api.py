@@ -18,6 +18,7 @@ _PREC = {"fp64": _lib.KNND_PREC_FP64, "mixed": _lib.KNND_PREC_MIXED_FP32,
          "mixed_fp32": _lib.KNND_PREC_MIXED_FP32, "bf16x3": _lib.KNND_PREC_MIXED_BF16X3,
          "auto": _lib.KNND_PREC_AUTO}
 _CMP = {"kl": _lib.KNND_CMP_KL, "kl_reverse": _lib.KNND_CMP_KL_REVERSE, "sqeuclidean": _lib.KNND_CMP_SQEUCLIDEAN}
+_LOOP = {"auto": _lib.KNND_LOOP_AUTO, "host": _lib.KNND_LOOP_HOST, "graph": _lib.KNND_LOOP_GRAPH}
 _DTYPE = {"f32": _lib.KNND_F32, "f64": _lib.KNND_F64, torch.float32: _lib.KNND_F32,
           torch.float64: _lib.KNND_F64}
 
@@ -49,13 +50,13 @@ class Handle:
     def __init__(self, n: int, m: int, K: int, dtype="f32", precision="mixed", fcc_samples: int = 10000,
                  max_rounds: int = 64, stop_on_zero_updates: bool = True, debug: bool = False,
                  timing: bool = False, incremental: bool = False, stop_delta: float = 0.0, comparator: str = "kl",
-                 stream=None):
+                 loop: str = "auto", stream=None):
         lib = _lib.load()
         self.n, self.m, self.K = n, m, K
         self.dtype = _DTYPE[dtype]
         self.torch_dtype = torch.float32 if self.dtype == _lib.KNND_F32 else torch.float64
         prm = _lib.knnd_params(fcc_samples, max_rounds, int(stop_on_zero_updates), int(debug), int(timing),
-                               int(incremental), float(stop_delta), _CMP[comparator])
+                               int(incremental), float(stop_delta), _CMP[comparator], _LOOP[loop])
         h = ctypes.c_void_p()
         check(lib.knnd_create(ctypes.byref(h), n, m, K, self.dtype, _PREC[precision], ctypes.byref(prm),
                               _stream_ptr(stream)), "knnd_create")

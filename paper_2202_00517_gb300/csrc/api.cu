@@ -40,6 +40,8 @@ knnd_status dalloc(knnd_handle *h, T **p, int64_t count)
     return KNND_OK;
 }
 
+void drop_loop_graph(knnd_handle *h);
+
 void free_all(knnd_handle *h)
 {
     void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg,
@@ -49,6 +51,10 @@ void free_all(knnd_handle *h)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->cnt_host) cudaFreeHost(h->cnt_host);
+    drop_loop_graph(h);
+    if (h->loop_st) cudaFree(h->loop_st);
+    if (h->loop_host) cudaFreeHost(h->loop_host);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->events_made)
         for (int i = 0; i < 2 * knnd_handle::kMaxPending; ++i)
             if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -130,8 +136,9 @@ knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
 }
 
 // G_{r-1} -> G_r in place; counters kCntUpdates/kCntRescored accumulate.
+// loop: a round of the device-driven loop (the FCC sample reads seed and round there).
 knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx, double *key, uint8_t *newflag,
-                     int64_t *fcc_hits)
+                     int64_t *fcc_hits, const LoopState *loop = nullptr)
 {
     // incremental proposals read the flags of G_{r-1} (the join runs before the
     // merge overwrites them with those of G_r)
@@ -151,12 +158,182 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
     }
     if (e == cudaSuccess && fcc_hits) {
         t = phase_begin(h, KNND_PHASE_FCC);
-        e = launch_fcc(h, idx, seed, round, fcc_hits);
+        e = launch_fcc(h, idx, seed, round, fcc_hits, loop);
         phase_end(h, t, KNND_PHASE_FCC);
     }
     h->round_flag = nullptr;
     h->rounds_run += 1;
     return cuda_status(e);
+}
+
+// ---- device-driven round loop (KNND_LOOP_GRAPH) ------------------------------
+// One graph per handle: [while cond] { loop_begin; round (CSR, join, merge,
+// FCC); loop_end }.  loop_end applies the host loop's stop rule, in the same
+// order and arithmetic, and sets the condition.
+
+struct LoopRule {
+    int32_t max_rounds;
+    int32_t stop_on_zero;
+    float stop_delta;
+    int64_t n;
+    int32_t K;
+};
+
+__global__ void loop_init_kernel(LoopState *st, unsigned long long seed, const int64_t *cnt)
+{
+    st->seed = seed;
+    st->round = 0;
+    st->stop_reason = 0;
+    st->hits[0] = cnt[kCntHits];
+    for (int i = 0; i < 5; ++i) st->sums[i] = 0;
+}
+
+__global__ void loop_begin_kernel(LoopState *st, int64_t *cnt)
+{
+    st->round += 1;
+    for (int i = 0; i < kCntNum; ++i) cnt[i] = 0;
+}
+
+__global__ void loop_end_kernel(LoopState *st, const int64_t *cnt, LoopRule rule, cudaGraphConditionalHandle cond)
+{
+    const int r = st->round;
+    const long long u = cnt[kCntUpdates], hits = cnt[kCntHits];
+    st->updates[r - 1] = u;
+    st->hits[r] = hits;
+    st->sums[0] += cnt[kCntRescored];
+    st->sums[1] += cnt[kCntBoundViol];
+    st->sums[2] += cnt[kCntFallback];
+    st->sums[3] += cnt[kCntSurvivors];
+    st->sums[4] += cnt[kCntAudited];
+    int reason = 0;
+    if (hits <= st->hits[r - 1]) reason = KNND_STOP_FCC;
+    else if (rule.stop_on_zero && u == 0) reason = KNND_STOP_ZERO;
+    else if (rule.stop_delta > 0.f && (double)u < (double)rule.stop_delta * (double)rule.n * (double)rule.K)
+        reason = KNND_STOP_DELTA;
+    else if (r >= rule.max_rounds) reason = KNND_STOP_MAX_ROUNDS;
+    st->stop_reason = reason;
+    cudaGraphSetConditional(cond, reason == 0 ? 1u : 0u);
+}
+
+void drop_loop_graph(knnd_handle *h)
+{
+    if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+    if (h->loop_graph) cudaGraphDestroy(h->loop_graph);
+    h->loop_exec = nullptr;
+    h->loop_graph = nullptr;
+    h->loop_for[0] = h->loop_for[1] = h->loop_for[2] = nullptr;
+}
+
+// Capture one round into the body of a while node (on the handle's own
+// capture stream: the caller's may be the legacy stream) and instantiate.
+knnd_status make_loop_graph(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag)
+{
+    drop_loop_graph(h);
+    if (!h->loop_st) {
+        if (cudaMalloc((void **)&h->loop_st, sizeof(LoopState)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            h->loop_st = nullptr;
+            return KNND_ENOMEM;
+        }
+        h->ws_bytes += sizeof(LoopState);
+    }
+    if (!h->loop_host && cudaMallocHost((void **)&h->loop_host, sizeof(LoopState)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->loop_host = nullptr;
+        return KNND_ENOMEM;
+    }
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return KNND_ECUDA;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_status(e);
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    const int64_t launches0 = h->launches;
+    const int64_t rounds0 = h->rounds_run;
+    knnd_status s = KNND_OK;
+    e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        loop_begin_kernel<<<1, 1, 0, h->cap_stream>>>(h->loop_st, h->cnt);
+        s = do_round(h, 0, 0, idx, key, newflag, h->cnt + kCntHits, h->loop_st);
+        LoopRule rule{h->prm.max_rounds, h->prm.stop_on_zero_updates, h->prm.stop_delta, h->n, h->K};
+        loop_end_kernel<<<1, 1, 0, h->cap_stream>>>(h->loop_st, h->cnt, rule, cond);
+        cudaGraph_t out = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &out);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = e2;
+    }
+    h->stream = user;
+    h->loop_round_launches = h->launches - launches0 + 2;
+    h->launches = launches0;
+    h->rounds_run = rounds0;
+    if (e == cudaSuccess && !s) e = cudaGraphInstantiate(&h->loop_exec, g, 0);
+    if (e != cudaSuccess || s) {
+        (void)cudaGetLastError();
+        cudaGraphDestroy(g);
+        h->loop_exec = nullptr;
+        return s ? s : cuda_status(e);
+    }
+    h->loop_graph = g;
+    h->loop_for[0] = idx;
+    h->loop_for[1] = key;
+    h->loop_for[2] = newflag;
+    return KNND_OK;
+}
+
+// The rounds of knnd_build with the stop rule on the device: G_0 and its hits
+// are in idx/key and cnt[kCntHits]; one graph launch runs every round.
+knnd_status graph_rounds(knnd_handle *h, uint64_t seed, int32_t *idx, double *key, uint8_t *newflag,
+                         knnd_build_info *info)
+{
+    if (!h->loop_exec || h->loop_for[0] != idx || h->loop_for[1] != key || h->loop_for[2] != newflag) {
+        const knnd_status s = make_loop_graph(h, idx, key, newflag);
+        if (s) return s;
+    }
+    loop_init_kernel<<<1, 1, 0, h->stream>>>(h->loop_st, seed, h->cnt);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->loop_exec, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->loop_host, h->loop_st, sizeof(LoopState), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const LoopState &st = *h->loop_host;
+    const int32_t R = st.round;
+    if (R < 1 || R > h->prm.max_rounds || st.stop_reason == 0) return KNND_ECUDA;  // the loop did not finish
+    info->rounds = R;
+    info->stop_reason = st.stop_reason;
+    for (int32_t r = 1; r <= R; ++r) {
+        info->updates[r - 1] = st.updates[r - 1];
+        info->fcc_hits[r] = st.hits[r];
+    }
+    info->rescored = st.sums[0];
+    info->bound_violations = st.sums[1];
+    info->merge_fallbacks = st.sums[2];
+    info->join_survivors = st.sums[3];
+    info->bound_audited = st.sums[4];
+    info->proposals = (int64_t)R * h->n * (int64_t)h->K * (2 * (int64_t)h->K + 1);
+    h->launches += 1 + (int64_t)R * h->loop_round_launches;
+    h->rounds_run += R;
+    return KNND_OK;
+}
+
+bool use_graph_loop(const knnd_handle *h)
+{
+    return h->prm.loop == KNND_LOOP_GRAPH || (h->prm.loop == KNND_LOOP_AUTO && !h->prm.timing);
 }
 
 }  // namespace
@@ -174,6 +351,7 @@ knnd_params default_params()
     p.incremental = 0;
     p.stop_delta = 0.f;
     p.comparator = KNND_CMP_KL;
+    p.loop = KNND_LOOP_AUTO;
     return p;
 }
 
@@ -326,6 +504,8 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
     if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_SQEUCLIDEAN) return KNND_EINVAL;
     if (prm.debug < 0 || prm.debug > 2) return KNND_EINVAL;
+    if (prm.loop < KNND_LOOP_AUTO || prm.loop > KNND_LOOP_GRAPH) return KNND_EINVAL;
+    if (prm.loop == KNND_LOOP_GRAPH && prm.timing) return KNND_EINVAL;  // event nodes cannot sit in the loop body
     // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
     if ((int64_t)K * K + (int64_t)(K + 1) * (n - 1) >= ((int64_t)1 << 31)) return KNND_EOVERFLOW;
     knnd::Caps caps;
@@ -426,11 +606,18 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
         e = launch_fcc(h, idx, seed, 0, d + kCntHits);
         phase_end(h, t, KNND_PHASE_FCC);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hst, d, sizeof(int64_t) * kCntNum, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    info->init_pairs = h->n * h->K;
+    if (use_graph_loop(h)) {
+        s = graph_rounds(h, seed, idx, key, newflag, info);
+        if (s) return s;
+        info->fcc_hits[0] = h->loop_host->hits[0];
+        return take_device_error(h);
+    }
+    e = cudaMemcpyAsync(hst, d, sizeof(int64_t) * kCntNum, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     info->fcc_hits[0] = hst[kCntHits];
-    info->init_pairs = h->n * h->K;
     const int64_t per_round = h->n * (int64_t)h->K * (2 * (int64_t)h->K + 1);
     int32_t r = 0;
     while (r < h->prm.max_rounds) {

@@ -134,6 +134,18 @@ struct __align__(16) RowMeta {
     long long boff;
 };
 
+// State of the device-driven round loop (KNND_LOOP_GRAPH), in device memory:
+// the round kernels read the seed and the round number from it, and the
+// loop's last kernel records the round's counters and the stop decision.
+struct LoopState {
+    unsigned long long seed;
+    int32_t round;        // rounds begun
+    int32_t stop_reason;  // KNND_STOP_* once the loop has stopped, else 0
+    long long updates[KNND_MAX_ROUNDS];
+    long long hits[KNND_MAX_ROUNDS + 1];
+    long long sums[5];  // rescored, bound violations, merge fallbacks, join survivors, audited pairs
+};
+
 // Device counters of one call (int64 each).
 enum Counter : int {
     kCntUpdates = 0,
@@ -220,6 +232,16 @@ struct knnd_handle {
     uint64_t *inst_seed;
     int32_t *inst_active;
     int64_t *inst_cnt;
+    // device-driven round loop (KNND_LOOP_GRAPH): state, pinned mirror, the
+    // stream the round is captured on, the graph and the pointers it was
+    // captured for, kernels per round in the graph
+    knnd::LoopState *loop_st;
+    knnd::LoopState *loop_host;
+    cudaStream_t cap_stream;
+    cudaGraph_t loop_graph;
+    cudaGraphExec_t loop_exec;
+    const void *loop_for[3];
+    int64_t loop_round_launches;
     // statistics
     int64_t launches;
     int64_t rounds_run;
@@ -241,7 +263,8 @@ cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx);
 double bound_c_bf16x3(int MP);
 bool tc_supported(int MP, int K);
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag);
-cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out);
+cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out,
+                       const LoopState *loop = nullptr);  // loop: seed and round read from it on the device
 
 // ---- handle set-up shared by the single-instance and batched forms ----
 struct Caps {

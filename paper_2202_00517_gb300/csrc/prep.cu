@@ -223,8 +223,12 @@ __device__ __forceinline__ bool row_has(const int32_t *__restrict__ idx, int K, 
 }
 
 __global__ void fcc_kernel(const int32_t *__restrict__ idx, int64_t n, int K, uint64_t seed, int32_t round,
-                           int32_t S, int64_t *hits, int32_t *err)
+                           int32_t S, int64_t *hits, int32_t *err, const LoopState *loop)
 {
+    if (loop) {  // a round of the device-driven loop
+        seed = loop->seed;
+        round = loop->round;
+    }
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     int hit = 0;
     if (s < S) {
@@ -288,13 +292,14 @@ cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round)
     return cudaGetLastError();
 }
 
-cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out)
+cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out,
+                       const LoopState *loop)
 {
     const int threads = 256;
     const int S = h->prm.fcc_samples;
     cudaMemsetAsync(hits_out, 0, sizeof(int64_t), h->stream);
     fcc_kernel<<<(S + threads - 1) / threads, threads, 0, h->stream>>>(idx, h->n, h->K, seed, round, S, hits_out,
-                                                                       h->err);
+                                                                       h->err, loop);
     h->launches += 1;
     return cudaGetLastError();
 }
