@@ -236,11 +236,11 @@ def gpu_single(args, name, rank, world, local, barrier):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
-    def run_form(prec, steps, warmup, clocks=None, incremental=False, loop="host"):
+    def run_form(prec, steps, warmup, clocks=None, incremental=False, loop="host", **kw):
         # host loop: per-phase CUDA events (the join's launch time for the roofline);
         # graph loop: one graph launch per build, no events inside it
         h = knnd.Handle(N, M, K, dtype="f32", precision=prec, timing=loop == "host", incremental=incremental,
-                        loop=loop)
+                        loop=loop, **kw)
         idx, key, flag = h.new_graph(dev)
         for _ in range(warmup):
             h.build(pts, SEED, idx, key, flag)
@@ -275,6 +275,15 @@ def gpu_single(args, name, rank, world, local, barrier):
     incr = run_form(args.form, 1, 1, incremental=True) if args.steps > 0 else None
     # the same build with the round loop on the device (CUDA graph with a while node)
     gloop = run_form(args.form, min(args.steps, 5), 1, loop="graph") if args.steps > 0 else None
+    # the options of the same build: the other join form, comparators, the delta stop
+    variants = {}
+    if args.steps > 0 and not args.no_variants:
+        vsteps = min(args.steps, 3)
+        other = "bf16x3" if args.form == "mixed" else "mixed"
+        for vname, prec, kw in ((other, other, {}), ("kl_reverse", args.form, {"comparator": "kl_reverse"}),
+                                ("sqeuclidean", args.form, {"comparator": "sqeuclidean"}),
+                                ("stop_delta_0.001", args.form, {"stop_delta": 0.001})):
+            variants[vname] = run_form(prec, vsteps, 1, **kw)
 
     # end to end through the public API from pinned host memory (H2D points, D2H idx+key)
     h = knnd.Handle(N, M, K, dtype="f32", precision=args.form)
@@ -368,6 +377,22 @@ def gpu_single(args, name, rank, world, local, barrier):
             "graph_launches_per_build": gloop["stats"]["kernel_launches"] / len(gloop["infos"]),
             "same_graph": bool(g_info["rounds"] == info["rounds"] and g_info["updates"] == info["updates"]
                                and torch.equal(g_info["idx"], info["idx"]) and torch.equal(g_info["key"], info["key"]))}
+    if variants:
+        line["variants"] = {}
+        for vname, v in variants.items():
+            vi = v["infos"][-1]
+            vst = v["stats"]
+            line["variants"][vname] = {
+                "build_s": v["ms"] / len(v["infos"]) / 1e3, "rounds": vi["rounds"],
+                "evals_per_s": world * v["evals"] / (v["ms"] / 1e3),
+                "join_ms_per_launch": vst["phase_ms"]["join"] / max(1, vst["phase_count"]["join"]),
+                "merge_ms_per_launch": vst["phase_ms"]["merge"] / max(1, vst["phase_count"]["merge"]),
+                "rescored_per_build": vi["rescored"]}
+        if other in variants:
+            oi = variants[other]["infos"][-1]
+            line["variants"][other]["same_graph"] = bool(
+                oi["rounds"] == info["rounds"] and torch.equal(oi["idx"], info["idx"])
+                and torch.equal(oi["key"], info["key"]))
     if fp64:
         line["build_s_fp64"] = fp64_ms / max(1, args.fp64_steps) / 1e3
         line["evals_per_s_fp64"] = world * fp64["evals"] / (fp64_ms / 1e3)
@@ -497,6 +522,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="n1e6_d20_K20", choices=list(WORKLOADS) + ["batch4096"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the option legs (other join form, comparators, delta stop)")
     ap.add_argument("--form", default="mixed", choices=["mixed", "bf16x3"],
                     help="headline mixed form: FP32 CUDA-core join or BF16x3 tcgen05 join")
     ap.add_argument("--batch-sample", type=int, default=256)

@@ -372,6 +372,31 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
                              "r"((uint32_t)Lay::TMEM_COLS));
 }
 
+// Resident CTAs per SM from the device's limits: shared memory (with the
+// per-block reservation), registers, threads, and TMEM (512 columns per SM,
+// each CTA holding `tmem_cols` for its lifetime).  The runtime's occupancy
+// query answers 1 for this kernel, which left the GPU with one hub in flight
+// per SM.
+static int tc_blocks_per_sm(const void *fn, size_t smem, int threads, int tmem_cols, int device)
+{
+    int smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, device);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp, 256 at a time
+    int n = 512 / tmem_cols;
+    n = std::min(n, smem_sm / (int)(smem + resv));
+    n = std::min(n, regs_sm / (regs_warp * (threads / 32)));
+    n = std::min(n, thr_sm / threads);
+    return std::max(n, 1);
+}
+
 template <int MP, int KD, int N>
 static cudaError_t run_tc(knnd_handle *h, const TcArgs &a)
 {
@@ -379,10 +404,10 @@ static cudaError_t run_tc(knnd_handle *h, const TcArgs &a)
     const int threads = 128;
     const size_t smem = Lay::BYTES;
     cudaFuncSetAttribute(join_tc_kernel<MP, KD, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_tc_kernel<MP, KD, N>, threads, smem);
-    if (per_sm < 1) per_sm = 1;
-    per_sm = std::min(per_sm, 512 / Lay::TMEM_COLS);  // TMEM: 512 columns per SM
+    cudaFuncSetAttribute(join_tc_kernel<MP, KD, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    const int per_sm =
+        tc_blocks_per_sm((const void *)join_tc_kernel<MP, KD, N>, smem, threads, Lay::TMEM_COLS, h->device);
     const int64_t grid = std::min<int64_t>(h->n, (int64_t)h->num_sms * per_sm);
     join_tc_kernel<MP, KD, N><<<(unsigned)grid, threads, smem, h->stream>>>(a);
     return cudaGetLastError();
