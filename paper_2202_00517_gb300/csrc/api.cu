@@ -230,12 +230,8 @@ knnd_status make_loop_graph(knnd_handle *h, int32_t *idx, double *key, uint8_t *
 {
     drop_loop_graph(h);
     if (!h->loop_st) {
-        if (cudaMalloc((void **)&h->loop_st, sizeof(LoopState)) != cudaSuccess) {
-            (void)cudaGetLastError();
-            h->loop_st = nullptr;
-            return KNND_ENOMEM;
-        }
-        h->ws_bytes += sizeof(LoopState);
+        const knnd_status s = dalloc(h, &h->loop_st, 1);
+        if (s) return s;
     }
     if (!h->loop_host && cudaMallocHost((void **)&h->loop_host, sizeof(LoopState)) != cudaSuccess) {
         (void)cudaGetLastError();

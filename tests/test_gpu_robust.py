@@ -1,7 +1,9 @@
 """Failure handling and resumption on the GPU, with no GPU fault:
 
 * a workspace allocation that fails (faked on the host, KNND_TEST_FAIL_ALLOC)
-  makes knnd_create return ENOMEM and frees everything it had allocated;
+  makes knnd_create return ENOMEM and frees everything it had allocated; a
+  failing allocation of the graph loop's state makes that build return ENOMEM
+  and leaves the handle usable;
 * checkpoint / resume: the state at a round boundary is (idx, key, new-flags,
   round number, seed); rounds continued from a saved state on a fresh handle
   reproduce the uninterrupted run bit for bit (the random draws are keyed by
@@ -49,6 +51,35 @@ def test_allocation_failure_frees_the_workspace(knnd):
     assert failures >= 5
     h = knnd.Handle(n, m, K, dtype="f32", precision="mixed")  # and the next one works
     h.close()
+
+
+def test_loop_state_allocation_failure(knnd):
+    # the graph loop allocates its state at the first build: a failure there is
+    # ENOMEM from that build, and the next build on the same handle succeeds
+    n, m, K, seed = 20_000, 11, 16, 3
+    pts = torch.from_numpy(dirichlet_points(n, m, seed, np.float32)).cuda()
+    h = None
+    try:
+        for at in range(1, 64):  # the first count create survives: its allocations + 1
+            os.environ["KNND_TEST_FAIL_ALLOC"] = str(at)
+            try:
+                h = knnd.Handle(n, m, K, dtype="f32", precision="mixed", loop="graph")
+                break
+            except knnd.api._lib.KnndError as e:
+                assert e.status == knnd.api._lib.KNND_ENOMEM
+        assert h is not None
+        with pytest.raises(knnd.api._lib.KnndError) as ei:
+            h.build(pts, seed)
+        assert ei.value.status == knnd.api._lib.KNND_ENOMEM
+    finally:
+        os.environ.pop("KNND_TEST_FAIL_ALLOC", None)
+    out = h.build(pts, seed)
+    h.close()
+    ref = knnd.Handle(n, m, K, dtype="f32", precision="mixed", loop="host")
+    r = ref.build(pts, seed)
+    ref.close()
+    assert out["rounds"] == r["rounds"] and out["updates"] == r["updates"]
+    assert torch.equal(out["idx"], r["idx"]) and torch.equal(out["key"], r["key"])
 
 
 @pytest.mark.parametrize("incremental", [False, True])
