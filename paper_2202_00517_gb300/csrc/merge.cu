@@ -130,6 +130,7 @@ struct MergeArgs {
     int64_t n;
     int K;
     int MP;
+    int M2;  // double2 elements holding the m coordinates, (m + 1) / 2: the re-score skips the rest of the padding
     int32_t *idx;
     double *key;
     uint8_t *flag;
@@ -233,23 +234,36 @@ __device__ __forceinline__ void flush_counts(const MergeArgs &a, int newcount, l
 }
 
 // Canonical FP64 key of (x, y): the same fma chain as the join and the
-// initial graph, with loads issued eight coordinates at a time.
+// initial graph.  TRIM (the one-entry-per-lane lists, K <= 32): the chain
+// stops at the first even count >= m, since the padding terms past m are exact
+// no-ops (0 * 0 added) and FP64 issue is scarce on this GPU; otherwise it runs
+// over the padded width, eight coordinates per step (fewer registers).
+template <bool TRIM>
 __device__ __forceinline__ double rescore(const MergeArgs &a, int64_t x, int y, double nh)
 {
     const double2 *xr = reinterpret_cast<const double2 *>(a.X64 + x * a.MP);
     const double2 *lr = reinterpret_cast<const double2 *>(a.L64 + (int64_t)y * a.MP);
     double acc = 0.0;
-    for (int i8 = 0; i8 < a.MP / 8; ++i8) {
-        double2 p[4], q[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            p[t] = __ldg(xr + 4 * i8 + t);
-            q[t] = __ldg(lr + 4 * i8 + t);
+    if (TRIM) {
+#pragma unroll 4
+        for (int i2 = 0; i2 < a.M2; ++i2) {
+            const double2 p = __ldg(xr + i2), q = __ldg(lr + i2);
+            acc = __fma_rn(p.x, q.x, acc);
+            acc = __fma_rn(p.y, q.y, acc);
         }
+    } else {
+        for (int i8 = 0; i8 < a.MP / 8; ++i8) {
+            double2 p[4], q[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            acc = __fma_rn(p[t].x, q[t].x, acc);
-            acc = __fma_rn(p[t].y, q[t].y, acc);
+            for (int t = 0; t < 4; ++t) {
+                p[t] = __ldg(xr + 4 * i8 + t);
+                q[t] = __ldg(lr + 4 * i8 + t);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                acc = __fma_rn(p[t].x, q[t].x, acc);
+                acc = __fma_rn(p[t].y, q[t].y, acc);
+            }
         }
     }
     return nh - acc;
@@ -258,12 +272,12 @@ __device__ __forceinline__ double rescore(const MergeArgs &a, int64_t x, int y, 
 // key(x, y) under the comparator CMP: KL negH(x) - <x, log y>; reverse KL the
 // same chain with the roles swapped; squared Euclidean (|x|^2 - 2 <x, y>) + |y|^2
 // (the tables then hold the coordinates and the squared norms).  nh: negH(x).
-template <int CMP>
+template <int CMP, bool TRIM>
 __device__ __forceinline__ double rescore_dir(const MergeArgs &a, int64_t x, int y, double nh)
 {
-    if (CMP == KNND_CMP_KL_REVERSE) return rescore(a, (int64_t)y, (int)x, a.negH[y]);
-    if (CMP == KNND_CMP_SQEUCLIDEAN) return (a.negH[x] + 2.0 * rescore(a, x, y, 0.0)) + a.negH[y];
-    return rescore(a, x, y, nh);
+    if (CMP == KNND_CMP_KL_REVERSE) return rescore<TRIM>(a, (int64_t)y, (int)x, a.negH[y]);
+    if (CMP == KNND_CMP_SQEUCLIDEAN) return (a.negH[x] + 2.0 * rescore<TRIM>(a, x, y, 0.0)) + a.negH[y];
+    return rescore<TRIM>(a, x, y, nh);
 }
 
 // ------------------------------------------------------------------ old-list set
@@ -369,7 +383,7 @@ __device__ void serial_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE>
         uint64_t k = 0;
         if (want) {
             if (MIXED) {
-                k = dkey(rescore_dir<CMP>(a, x, ci, B.nh));
+                k = dkey(rescore_dir<CMP, NE == 1>(a, x, ci, B.nh));
                 rescored += 1;
             } else {
                 k = dkey(a.bkey[base + c0 + lane]);
@@ -586,7 +600,7 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
             const int2 e = live_list[c0 + lane];
             ci = e.x;
             if (MIXED) {
-                k = dkey(rescore_dir<CMP>(a, x, ci, B.nh));
+                k = dkey(rescore_dir<CMP, NE == 1>(a, x, ci, B.nh));
                 rescored += 1;
             } else {
                 k = dkey(a.bkey[base + e.y]);
@@ -693,6 +707,7 @@ cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *new
     a.n = h->n;
     a.K = h->K;
     a.MP = h->MP;
+    a.M2 = (h->m + 1) / 2;
     a.idx = idx;
     a.key = key;
     a.flag = newflag;
