@@ -109,6 +109,8 @@ SHAPES = [
     (600, 128, 64, 8, "f64"),
     (2500, 24, 20, 9, "f32"),
     (1200, 40, 17, 10, "f32"),   # 40 coordinates (48 padded), odd K
+    (1300, 19, 20, 11, "f32"),   # 19 coordinates (24 padded)
+    (900, 10, 40, 12, "f64"),    # 10 coordinates (16 padded) with K > 32
 ]
 
 
