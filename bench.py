@@ -42,6 +42,9 @@ WORKLOADS = {
                                             "d=20 (21 FP32 coords), K=20, seed 1"),
     "n4e6_d64_K32": (4_000_000, 65, 32, 2, "KL K-NN descent build to the statistical stop, n=4e6 Dirichlet(1) points, "
                                             "d=64 (65 FP32 coords), K=32, seed 2"),
+    # the paper's largest Table 3 run (Sec. 4.4: 9-simplex, n = 2e6, K = 16)
+    "n2e6_d9_K16": (2_000_000, 10, 16, 3, "KL K-NN descent build to the statistical stop, n=2e6 Dirichlet(1) points, "
+                                          "d=9 (10 FP32 coords), K=16, seed 3 (Table 3 shape)"),
     # profiling-size case of the benchmark shape: the join's gather set (n x 208 B)
     # still exceeds the 129 MB L2, while the device holds about 6 GB
     "n8e5_d20_K20": (800_000, 21, 20, 1, "KL K-NN descent build to the statistical stop, n=8e5 Dirichlet(1) points, "
