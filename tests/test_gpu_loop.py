@@ -154,3 +154,36 @@ def test_graph_loop_reports_device_errors(knnd):
     out = h.build(_dev(good), 19)  # the handle stays usable
     h.close()
     assert out["rounds"] >= 1
+
+
+@pytest.mark.parametrize("n,m,K,kw", [
+    (3, 2, 2, {}),                      # the smallest problem
+    (500, 6, 10, {"max_rounds": 1}),    # one round: the cap stops it
+    (2000, 6, 10, {"fcc_samples": 1}),
+    (1500, 65, 33, {}),                 # K > 32
+])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_edge_cases(knnd, n, m, K, kw, prec):
+    pts = _dev(dirichlet_points(n, m, 21, np.float64))
+    a, b = _both(knnd, pts, K, 21, precision=prec, **kw)
+    _same(a, b)
+    if kw.get("max_rounds") == 1:
+        assert b["rounds"] == 1 and b["stop_reason"] in (knnd.api._lib.KNND_STOP_MAX_ROUNDS,
+                                                          knnd.api._lib.KNND_STOP_FCC,
+                                                          knnd.api._lib.KNND_STOP_ZERO)
+
+
+def test_graph_loop_on_a_side_stream(knnd):
+    # the graph is launched on the handle's stream, whatever stream captured it
+    n, m, K = 5000, 11, 16
+    pts = _dev(dirichlet_points(n, m, 23, np.float32))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        h = knnd.Handle(n, m, K, dtype="f32", precision="mixed", loop="graph", stream=s)
+        out = h.build(pts, 23)
+        s.synchronize()
+        h.close()
+    ref = knnd.Handle(n, m, K, dtype="f32", precision="mixed", loop="host")
+    r = ref.build(pts, 23)
+    ref.close()
+    _same(r, out)
