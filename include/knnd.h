@@ -35,8 +35,10 @@
  *   - Work is enqueued on the handle's stream (a cudaStream_t passed as
  *     void*; NULL = the legacy default stream).  Calls that return a host
  *     value synchronise that stream; the others are stream-ordered.
- *   - Scratch memory lives in the handle: it is allocated by knnd_create and
- *     released by knnd_destroy.  Calls on one handle must not overlap.
+ *   - Scratch memory lives in the handle: it is allocated by knnd_create
+ *     (the graph round loop's small state and its CUDA graph by the first
+ *     knnd_build that uses them) and released by knnd_destroy.  Calls on one
+ *     handle must not overlap.
  *   - Every call returns a knnd_status.  Arguments are validated on the host
  *     before any launch; on an error nothing is enqueued unless stated.
  *     No C++ exception crosses this interface.
