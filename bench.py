@@ -315,15 +315,17 @@ def gpu_single(args, name, rank, world, local, barrier):
     # FP32 coordinates or logs per row and column of every hub tile, so HBM
     # gather traffic bounds it.  Algorithmic bytes per launch: per hub
     # (K + indeg) rows x (4 MP + 16) + K columns x (4 MP + 4) + (4 MP + 16), summed
-    # over hubs (sum of indeg = nK), plus 8 B per survivor written.
+    # over hubs (sum of indeg = nK), plus 8 B per survivor written.  Every round
+    # takes every hub once; the first round's hubs run in two launches (split
+    # round), so the per-launch figures average over all the timed launches.
     join_ms = st["phase_ms"]["join"]
     join_n = max(1, st["phase_count"]["join"])
     join_avg_s = join_ms / join_n / 1e3
     MP = pad_m(M)
     gather = N * ((2 * K + 1) * (4 * MP + 16) + K * (4 * MP + 4))
-    surv = sum(o["join_survivors"] for o in mixed["infos"]) / max(1, sum(o["rounds"] for o in mixed["infos"]))
-    bytes_per_launch = gather + 8.0 * surv
-    flops_per_launch = 2.0 * M * N * K * (2 * K + 1)
+    rounds_t = sum(o["rounds"] for o in mixed["infos"])
+    bytes_per_launch = (rounds_t * gather + 8.0 * sum(o["join_survivors"] for o in mixed["infos"])) / join_n
+    flops_per_launch = 2.0 * M * N * K * (2 * K + 1) * rounds_t / join_n
     peaks, peak_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     fp32_peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12  # TFLOP/s at the maximum SM clock

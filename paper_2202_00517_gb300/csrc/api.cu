@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -46,7 +47,8 @@ void free_all(knnd_handle *h)
 {
     void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg,
                     h->cof_off, h->cof, h->cof_new, h->flag_tmp, h->scan_tmp, h->tau, h->idxK, h->meta, h->Ex, h->bcnt, h->bkey,
-                    h->bent, h->fb_list, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev,
+                    h->bent, h->fb_list, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev, h->idxA, h->keyA,
+                    h->flagA,
                     h->inst_of, h->inst_base, h->inst_n, h->inst_seed, h->inst_active, h->inst_cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -136,6 +138,19 @@ knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
 }
 
 // G_{r-1} -> G_r in place; counters kCntUpdates/kCntRescored accumulate.
+// Split first round.  Round 1 proposes nearly its whole pool (the K-th of K
+// random friends is a poor threshold), so it runs in two phases: the hubs
+// [0, n / kSplitDen) propose and their candidates are merged into a copy of the
+// graph; every row's K-th entry there is an upper bound of its K-th key at the
+// end of the round (any part of the pool gives one), so the remaining hubs
+// propose against that tighter threshold, and their candidates are merged into
+// the copy to give G_1.  The graph, keys, flags and update count are those of
+// the one-phase round: the same pool, the same K best.  Measured: 3 % (n = 1e6,
+// m = 21, K = 20) to 5 % (m = 65, K = 32) off a build; splitting later rounds,
+// whose thresholds are already good, cost more than it saved.
+constexpr int32_t kSplitRounds = 1;
+constexpr int64_t kSplitDen = 8;
+
 // loop: a round of the device-driven loop (the FCC sample reads seed and round there).
 knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx, double *key, uint8_t *newflag,
                      int64_t *fcc_hits, const LoopState *loop = nullptr)
@@ -143,18 +158,36 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
     // incremental proposals read the flags of G_{r-1} (the join runs before the
     // merge overwrites them with those of G_r)
     h->round_flag = (h->prm.incremental && newflag) ? newflag : nullptr;
+    const bool split = h->idxA && round >= 1 && round <= kSplitRounds;
+    const int64_t hs = split ? std::max<int64_t>(1, h->n / kSplitDen) : h->n;
     int t = phase_begin(h, KNND_PHASE_CSR);
     cudaError_t e = launch_reverse_csr(h, idx, key);
     phase_end(h, t, KNND_PHASE_CSR);
     if (e == cudaSuccess) {
         t = phase_begin(h, KNND_PHASE_JOIN);
-        e = launch_join(h, idx);
+        e = launch_join(h, idx, 0, hs);
         phase_end(h, t, KNND_PHASE_JOIN);
     }
     if (e == cudaSuccess) {
         t = phase_begin(h, KNND_PHASE_MERGE);
-        e = launch_merge(h, idx, key, newflag);
+        e = split ? launch_merge_from(h, idx, key, nullptr, h->idxA, h->keyA, h->flagA, false)
+                  : launch_merge(h, idx, key, newflag);
         phase_end(h, t, KNND_PHASE_MERGE);
+    }
+    if (split && e == cudaSuccess) {
+        t = phase_begin(h, KNND_PHASE_CSR);
+        e = launch_thresholds(h, h->idxA, h->keyA);
+        phase_end(h, t, KNND_PHASE_CSR);
+        if (e == cudaSuccess) {
+            t = phase_begin(h, KNND_PHASE_JOIN);
+            e = launch_join(h, idx, hs, h->n);
+            phase_end(h, t, KNND_PHASE_JOIN);
+        }
+        if (e == cudaSuccess) {
+            t = phase_begin(h, KNND_PHASE_MERGE);
+            e = launch_merge_from(h, h->idxA, h->keyA, h->flagA, idx, key, newflag, true);
+            phase_end(h, t, KNND_PHASE_MERGE);
+        }
     }
     if (e == cudaSuccess && fcc_hits) {
         t = phase_begin(h, KNND_PHASE_FCC);
@@ -240,41 +273,55 @@ knnd_status make_loop_graph(knnd_handle *h, int32_t *idx, double *key, uint8_t *
     }
     if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return KNND_ECUDA;
+    // [round 1 (split), its stop test] -> while (condition set by the stop tests)
+    // { round, stop test }: the first round's stop test sets the while node's
+    // condition before the node is reached
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return cuda_status(e);
     cudaGraphConditionalHandle cond;
-    e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    e = cudaGraphConditionalHandleCreate(&cond, g, 0, 0);
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    const int64_t launches0 = h->launches;
+    const int64_t rounds0 = h->rounds_run;
+    const LoopRule rule{h->prm.max_rounds, h->prm.stop_on_zero_updates, h->prm.stop_delta, h->n, h->K};
+    knnd_status s = KNND_OK;
+    std::vector<cudaGraphNode_t> tail;
+    auto capture = [&](cudaGraph_t into, const cudaGraphNode_t *deps, size_t ndeps, int32_t round,
+                       bool keep_tail) -> cudaError_t {
+        cudaError_t c = cudaStreamBeginCaptureToGraph(h->cap_stream, into, deps, nullptr, ndeps,
+                                                      cudaStreamCaptureModeThreadLocal);
+        if (c != cudaSuccess) return c;
+        loop_begin_kernel<<<1, 1, 0, h->cap_stream>>>(h->loop_st, h->cnt);
+        const knnd_status rs = do_round(h, 0, round, idx, key, newflag, h->cnt + kCntHits, h->loop_st);
+        if (rs && !s) s = rs;
+        loop_end_kernel<<<1, 1, 0, h->cap_stream>>>(h->loop_st, h->cnt, rule, cond);
+        if (keep_tail) {
+            cudaStreamCaptureStatus st;
+            const cudaGraphNode_t *d = nullptr;
+            size_t nd = 0;
+            c = cudaStreamGetCaptureInfo(h->cap_stream, &st, nullptr, nullptr, &d, nullptr, &nd);
+            if (c == cudaSuccess) tail.assign(d, d + nd);
+        }
+        cudaGraph_t out = nullptr;
+        const cudaError_t c2 = cudaStreamEndCapture(h->cap_stream, &out);
+        c = c == cudaSuccess ? cudaGetLastError() : c;
+        return c == cudaSuccess ? c2 : c;
+    };
+    if (e == cudaSuccess) e = capture(g, nullptr, 0, 1, true);
+    const int64_t launches1 = h->launches;
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = cond;
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
     cudaGraphNode_t node;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return cuda_status(e);
-    }
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    cudaStream_t user = h->stream;
-    h->stream = h->cap_stream;
-    const int64_t launches0 = h->launches;
-    const int64_t rounds0 = h->rounds_run;
-    knnd_status s = KNND_OK;
-    e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        loop_begin_kernel<<<1, 1, 0, h->cap_stream>>>(h->loop_st, h->cnt);
-        s = do_round(h, 0, 0, idx, key, newflag, h->cnt + kCntHits, h->loop_st);
-        LoopRule rule{h->prm.max_rounds, h->prm.stop_on_zero_updates, h->prm.stop_delta, h->n, h->K};
-        loop_end_kernel<<<1, 1, 0, h->cap_stream>>>(h->loop_st, h->cnt, rule, cond);
-        cudaGraph_t out = nullptr;
-        const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &out);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = e2;
-    }
+    if (e == cudaSuccess && !s) e = cudaGraphAddNode(&node, g, tail.data(), nullptr, tail.size(), &np);
+    if (e == cudaSuccess && !s) e = capture(np.conditional.phGraph_out[0], nullptr, 0, kSplitRounds + 1, false);
     h->stream = user;
-    h->loop_round_launches = h->launches - launches0 + 2;
+    h->loop_first_launches = launches1 - launches0 + 2;
+    h->loop_round_launches = h->launches - launches1 + 2;
     h->launches = launches0;
     h->rounds_run = rounds0;
     if (e == cudaSuccess && !s) e = cudaGraphInstantiate(&h->loop_exec, g, 0);
@@ -322,7 +369,7 @@ knnd_status graph_rounds(knnd_handle *h, uint64_t seed, int32_t *idx, double *ke
     info->join_survivors = st.sums[3];
     info->bound_audited = st.sums[4];
     info->proposals = (int64_t)R * h->n * (int64_t)h->K * (2 * (int64_t)h->K + 1);
-    h->launches += 1 + (int64_t)R * h->loop_round_launches;
+    h->launches += 1 + h->loop_first_launches + (int64_t)(R - 1) * h->loop_round_launches;
     h->rounds_run += R;
     return KNND_OK;
 }
@@ -413,6 +460,9 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
     if (!s) s = dalloc(h, &h->fb_list, n);
     if (!s) s = dalloc(h, &h->fb_count, 1);
     if (!s) s = dalloc(h, &h->cnt, kCntNum);
+    if (!s && c.ninst == 0) s = dalloc(h, &h->idxA, c.nK);  // split rounds (single instance)
+    if (!s && c.ninst == 0) s = dalloc(h, &h->keyA, c.nK);
+    if (!s && c.ninst == 0) s = dalloc(h, &h->flagA, c.nK);
     if (!s && cudaMallocHost((void **)&h->cnt_host, sizeof(int64_t) * kCntNum) != cudaSuccess) s = KNND_ENOMEM;
     if (!s && c.ninst > 0) {
         if (!s) s = dalloc(h, &h->inst_of, n);

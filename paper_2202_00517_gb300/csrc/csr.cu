@@ -6,6 +6,50 @@
 
 namespace knnd {
 
+// Row x's join thresholds from its K-th entry (key t, index v): tau, idxK and,
+// mixed form, the FP32 rejection threshold phi and the error bound Ex.
+__device__ __forceinline__ void row_thresholds(int64_t x, double t, int32_t v, double *__restrict__ tau,
+                                               int32_t *__restrict__ idxK, const double *__restrict__ negH,
+                                               const double *__restrict__ nx,
+                                               const unsigned long long *__restrict__ smax_bits, const InstView &iv,
+                                               double bound_c, int cmp, RowMeta *__restrict__ meta,
+                                               double *__restrict__ Ex)
+{
+    tau[x] = t;
+    idxK[x] = v;
+    if (meta && cmp == KNND_CMP_KL) {
+        // |fp32 dot - fp64 dot| <= c_m * sum_i |x_i||log y_i| <= c_m * nx(x) * max|log|.
+        // margin covers the FP64 roundings of the key and threshold arithmetic.
+        const double smax = __longlong_as_double((long long)smax_bits[3 * iv.at(x)]);
+        const double nh = negH[x];
+        const double margin = 0x1p-40 * (fabs(nh) + nx[x] * smax + 1.0);
+        const double E = bound_c * nx[x] * smax + 0x1p-100 + margin;
+        Ex[x] = E;
+        meta[x].phi = __double2float_rd(nh - t - E);
+    } else if (meta) {
+        // comparators with a column offset, key(x, y) = ro(x) - s <R(x), C(y)> + co(y):
+        // reverse KL (ro = 0, co = negH(y), s = 1, R = log x, C = y) and squared
+        // Euclidean (ro = |x|^2, co = |y|^2, s = 2, R = x, C = y).  The tile's FP32
+        // dot d~ is off by at most c_m * sum_i |R_i||C_i| (+ underflow) <=
+        // E1 = c_m * max sum_j |y_j| * max |table entry|, per instance.  The join rejects
+        // y when d~ < RD(RD(co(y)/s) - phi) with phi = RU((tau - ro)/s + E1 + margin),
+        // which proves key > tau.  The candidate's entry is u = s RN(RD(co(y)/s) - d~),
+        // and |ro + u - key| <= s E1 + 2^-22 (max|co| + s max sum|y| max|C| + 1) + margin
+        // covers the roundings of co/s, of the subtraction and of u: the merge bounds
+        // keys by ro + u +- Ex.
+        const unsigned long long *mx = smax_bits + 3 * (int64_t)iv.at(x);
+        const double smax = __longlong_as_double((long long)mx[0]);
+        const double hmax = __longlong_as_double((long long)mx[1]);
+        const double nmax = __longlong_as_double((long long)mx[2]);
+        const double sc = cmp == KNND_CMP_SQEUCLIDEAN ? 2.0 : 1.0;
+        const double ro = cmp == KNND_CMP_SQEUCLIDEAN ? negH[x] : 0.0;
+        const double E1 = bound_c * nmax * smax + 0x1p-100;
+        const double margin = 0x1p-40 * (fabs(t) + fabs(ro) + hmax + sc * nmax * smax + 1.0);
+        Ex[x] = sc * E1 + 0x1p-22 * (hmax + sc * nmax * smax + 1.0) + margin;
+        meta[x].phi = __double2float_ru((t - ro) / sc + E1 + margin);
+    }
+}
+
 // One thread per arc e = x*K + t (x -> idx[e]).
 __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *__restrict__ key, int64_t n, int K,
                                  int32_t *__restrict__ deg, double *__restrict__ tau, int32_t *__restrict__ idxK,
@@ -22,43 +66,22 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
     } else {
         atomicAdd(&deg[v], 1);
     }
-    if (e % K == K - 1) {
-        const int64_t x = e / K;
-        const double t = key[e];
-        tau[x] = t;
-        idxK[x] = v;
-        if (meta && cmp == KNND_CMP_KL) {
-            // |fp32 dot - fp64 dot| <= c_m * sum_i |x_i||log y_i| <= c_m * nx(x) * max|log|.
-            // margin covers the FP64 roundings of the key and threshold arithmetic.
-            const double smax = __longlong_as_double((long long)smax_bits[3 * iv.at(x)]);
-            const double nh = negH[x];
-            const double margin = 0x1p-40 * (fabs(nh) + nx[x] * smax + 1.0);
-            const double E = bound_c * nx[x] * smax + 0x1p-100 + margin;
-            Ex[x] = E;
-            meta[x].phi = __double2float_rd(nh - t - E);
-        } else if (meta) {
-            // comparators with a column offset, key(x, y) = ro(x) - s <R(x), C(y)> + co(y):
-            // reverse KL (ro = 0, co = negH(y), s = 1, R = log x, C = y) and squared
-            // Euclidean (ro = |x|^2, co = |y|^2, s = 2, R = x, C = y).  The tile's FP32
-            // dot d~ is off by at most c_m * sum_i |R_i||C_i| (+ underflow) <=
-            // E1 = c_m * max sum_j |y_j| * max |table entry|, per instance.  The join rejects
-            // y when d~ < RD(RD(co(y)/s) - phi) with phi = RU((tau - ro)/s + E1 + margin),
-            // which proves key > tau.  The candidate's entry is u = s RN(RD(co(y)/s) - d~),
-            // and |ro + u - key| <= s E1 + 2^-22 (max|co| + s max sum|y| max|C| + 1) + margin
-            // covers the roundings of co/s, of the subtraction and of u: the merge bounds
-            // keys by ro + u +- Ex.
-            const unsigned long long *mx = smax_bits + 3 * (int64_t)iv.at(x);
-            const double smax = __longlong_as_double((long long)mx[0]);
-            const double hmax = __longlong_as_double((long long)mx[1]);
-            const double nmax = __longlong_as_double((long long)mx[2]);
-            const double sc = cmp == KNND_CMP_SQEUCLIDEAN ? 2.0 : 1.0;
-            const double ro = cmp == KNND_CMP_SQEUCLIDEAN ? negH[x] : 0.0;
-            const double E1 = bound_c * nmax * smax + 0x1p-100;
-            const double margin = 0x1p-40 * (fabs(t) + fabs(ro) + hmax + sc * nmax * smax + 1.0);
-            Ex[x] = sc * E1 + 0x1p-22 * (hmax + sc * nmax * smax + 1.0) + margin;
-            meta[x].phi = __double2float_ru((t - ro) / sc + E1 + margin);
-        }
-    }
+    if (e % K == K - 1)
+        row_thresholds(e / K, key[e], v, tau, idxK, negH, nx, smax_bits, iv, bound_c, cmp, meta, Ex);
+}
+
+// The thresholds alone, from another graph of the same rows (the second phase
+// of a split round): one thread per row.
+__global__ void thresholds_kernel(const int32_t *__restrict__ idx, const double *__restrict__ key, int64_t n, int K,
+                                  double *__restrict__ tau, int32_t *__restrict__ idxK, const double *__restrict__ negH,
+                                  const double *__restrict__ nx, const unsigned long long *__restrict__ smax_bits,
+                                  InstView iv, double bound_c, int cmp, RowMeta *__restrict__ meta,
+                                  double *__restrict__ Ex)
+{
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const int64_t e = x * K + (K - 1);
+    row_thresholds(x, key[e], idx[e], tau, idxK, negH, nx, smax_bits, iv, bound_c, cmp, meta, Ex);
 }
 
 // Exclusive scan of the int32 degrees into int64 offsets, in three passes over
@@ -180,6 +203,17 @@ cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double 
     csr_fill_kernel<<<eblocks, threads, 0, h->stream>>>(idx, n, K, h->cof_off, h->deg, h->cof, h->round_flag,
                                                         h->cof_new);
     h->launches += 5;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thresholds(knnd_handle *h, const int32_t *idx, const double *key)
+{
+    const int threads = 256;
+    const bool mixed = h->prec != KNND_PREC_FP64;
+    thresholds_kernel<<<(unsigned)((h->n + threads - 1) / threads), threads, 0, h->stream>>>(
+        idx, key, h->n, h->K, h->tau, h->idxK, h->negH, h->nx, h->smax_bits, h->iv, h->bound_c, h->prm.comparator,
+        mixed ? h->meta : nullptr, h->Ex);
+    h->launches += 1;
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ namespace knnd {
 
 struct JoinArgs {
     int64_t n;
+    int64_t h_lo, h_hi;  // the hubs this launch takes: [h_lo, h_hi)
     int K;
     const int32_t *idx;
     const int64_t *cof_off;
@@ -144,15 +145,15 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
     const bool fast = MP <= 32 && K <= 32;
     const int CS = (K * (MP + 4) <= 32 * DS) ? MP + 4 : MP;
     const int64_t vstep = (int64_t)gridDim.x * wpb;
-    int64_t v = (int64_t)blockIdx.x * wpb + warp;
+    int64_t v = a.h_lo + (int64_t)blockIdx.x * wpb + warp;
     int64_t nc0 = 0, nc1 = 0;
-    if (v < n) {
+    if (v < a.h_hi) {
         nc0 = a.cof_off[v];
         nc1 = a.cof_off[v + 1];
     }
-    for (; v < n; v += vstep) {
+    for (; v < a.h_hi; v += vstep) {
         const int64_t c0 = nc0, c1 = nc1;
-        if (v + vstep < n) {
+        if (v + vstep < a.h_hi) {
             nc0 = a.cof_off[v + vstep];
             nc1 = a.cof_off[v + vstep + 1];
         }
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
     const int64_t n = a.n;
     const unsigned FULL = 0xffffffffu;
 
-    for (int64_t v = (int64_t)blockIdx.x * wpb + warp; v < n; v += (int64_t)gridDim.x * wpb) {
+    for (int64_t v = a.h_lo + (int64_t)blockIdx.x * wpb + warp; v < a.h_hi; v += (int64_t)gridDim.x * wpb) {
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
         int cid[CPL], cnew[CPL];
         double cnh[CPL];  // column offsets (reverse KL: negH(y); squared Euclidean: |y|^2)
@@ -627,8 +628,8 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_fp64_kernel<MP, CPL>, threads, smem);
         if (per_sm < 1) per_sm = 1;
-        const int64_t need = (h->n + threads / 32 - 1) / (threads / 32);
-        const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * per_sm);
+        const int64_t need = (a.h_hi - a.h_lo + threads / 32 - 1) / (threads / 32);
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)h->num_sms * per_sm));
         join_fp64_kernel<MP, CPL><<<(unsigned)grid, threads, smem, h->stream>>>(a);
     } else {
         using S = MixedSmem<MP>;
@@ -641,8 +642,8 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (per_sm < 1) per_sm = 1;
-        const int64_t need = (h->n + threads / 32 - 1) / (threads / 32);
-        const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * per_sm);
+        const int64_t need = (a.h_hi - a.h_lo + threads / 32 - 1) / (threads / 32);
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)h->num_sms * per_sm));
         kern<<<(unsigned)grid, threads, smem, h->stream>>>(a);
     }
     return cudaGetLastError();
@@ -655,12 +656,14 @@ static cudaError_t run_join_cpl(knnd_handle *h, const JoinArgs &a)
     return run_join<MP, 2>(h, a);
 }
 
-cudaError_t launch_join(knnd_handle *h, const int32_t *idx)
+cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi)
 {
     if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && h->prm.comparator == KNND_CMP_KL)
-        return launch_join_tc(h, idx);
+        return launch_join_tc(h, idx, h_lo, h_hi);
     JoinArgs a;
     a.n = h->n;
+    a.h_lo = h_lo;
+    a.h_hi = h_hi;
     a.K = h->K;
     a.idx = idx;
     a.cof_off = h->cof_off;

@@ -32,6 +32,7 @@ namespace knnd {
 
 struct TcArgs {
     int64_t n;
+    int64_t h_lo, h_hi;  // the hubs this launch takes: [h_lo, h_hi)
     int K;
     const int32_t *idx;
     const int64_t *cof_off;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
     int64_t *sRB = reinterpret_cast<int64_t *>(sInc + 32);
     int64_t ndot = 0, nviol = 0;
 
-    for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
+    for (int64_t v = a.h_lo + blockIdx.x; v < a.h_hi; v += gridDim.x) {
         if (!a.iv.live(v)) continue;
         // columns: F(v), then v itself (the co-friend column of the rows of F(v))
         for (int j = t; j < N; j += blockDim.x) {
@@ -408,7 +409,7 @@ static cudaError_t run_tc(knnd_handle *h, const TcArgs &a)
                          cudaSharedmemCarveoutMaxShared);
     const int per_sm =
         tc_blocks_per_sm((const void *)join_tc_kernel<MP, KD, N>, smem, threads, Lay::TMEM_COLS, h->device);
-    const int64_t grid = std::min<int64_t>(h->n, (int64_t)h->num_sms * per_sm);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.h_hi - a.h_lo, (int64_t)h->num_sms * per_sm));
     join_tc_kernel<MP, KD, N><<<(unsigned)grid, threads, smem, h->stream>>>(a);
     return cudaGetLastError();
 }
@@ -426,10 +427,12 @@ static cudaError_t run_tc_n(knnd_handle *h, const TcArgs &a)
 
 bool tc_supported(int MP, int K) { return MP >= 8 && MP <= 128 && K + 1 <= 80; }
 
-cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx)
+cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi)
 {
     TcArgs a;
     a.n = h->n;
+    a.h_lo = h_lo;
+    a.h_hi = h_hi;
     a.K = h->K;
     a.idx = idx;
     a.cof_off = h->cof_off;

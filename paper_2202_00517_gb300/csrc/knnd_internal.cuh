@@ -215,6 +215,10 @@ struct knnd_handle {
     int64_t pts_dev_bytes;
     int32_t *idx_dev;
     double *key_dev;
+    // the graph after the first phase of a split round (single instance only)
+    int32_t *idxA;
+    double *keyA;
+    uint8_t *flagA;
     // per-phase CUDA-event timing (params.timing)
     static constexpr int kMaxPending = 256;
     cudaEvent_t ev[2 * kMaxPending];
@@ -234,13 +238,14 @@ struct knnd_handle {
     int64_t *inst_cnt;
     // device-driven round loop (KNND_LOOP_GRAPH): state, pinned mirror, the
     // stream the round is captured on, the graph and the pointers it was
-    // captured for, kernels per round in the graph
+    // captured for, kernels of its first round and of each later round
     knnd::LoopState *loop_st;
     knnd::LoopState *loop_host;
     cudaStream_t cap_stream;
     cudaGraph_t loop_graph;
     cudaGraphExec_t loop_exec;
     const void *loop_for[3];
+    int64_t loop_first_launches;
     int64_t loop_round_launches;
     // statistics
     int64_t launches;
@@ -258,11 +263,14 @@ cudaError_t launch_precompute_from(knnd_handle *h, const void *points, int64_t l
 cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round);
 cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, double *key, uint8_t *newflag);
 cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key);
-cudaError_t launch_join(knnd_handle *h, const int32_t *idx);
-cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx);
+cudaError_t launch_thresholds(knnd_handle *h, const int32_t *idx, const double *key);
+cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi);
+cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi);
 double bound_c_bf16x3(int MP);
 bool tc_supported(int MP, int K);
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag);
+cudaError_t launch_merge_from(knnd_handle *h, const int32_t *in_idx, const double *in_key, const uint8_t *in_flag,
+                              int32_t *idx, double *key, uint8_t *newflag, bool count);
 cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_t round, int64_t *hits_out,
                        const LoopState *loop = nullptr);  // loop: seed and round read from it on the device
 

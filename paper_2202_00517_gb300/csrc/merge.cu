@@ -131,9 +131,16 @@ struct MergeArgs {
     int K;
     int MP;
     int M2;  // double2 elements holding the m coordinates, (m + 1) / 2: the re-score skips the rest of the padding
+    // the rows merged (read) and the rows written; in_flag marks entries already new
+    // against the graph of the round's start (the second phase of a split round),
+    // or NULL (every entry read is old); count: add the new entries to the update count
+    const int32_t *in_idx;
+    const double *in_key;
+    const uint8_t *in_flag;
     int32_t *idx;
     double *key;
     uint8_t *flag;
+    int count;
     const int64_t *cof_off;
     const int32_t *bcnt;
     const int2 *bent;
@@ -162,7 +169,7 @@ __device__ __forceinline__ void flush_row_counts(const MergeArgs &a, int64_t x, 
     }
     if ((threadIdx.x & 31) == 0) {
         int64_t *c = a.iv.cnt + (int64_t)a.iv.of[x] * kCntNum;
-        if (nc) atomicAdd((unsigned long long *)&c[kCntUpdates], (unsigned long long)nc);
+        if (nc && a.count) atomicAdd((unsigned long long *)&c[kCntUpdates], (unsigned long long)nc);
         if (rs) atomicAdd((unsigned long long *)&c[kCntRescored], (unsigned long long)rs);
         if (fb) atomicAdd((unsigned long long *)&c[kCntFallback], (unsigned long long)fb);
     }
@@ -194,13 +201,14 @@ __device__ __forceinline__ void load_row(const MergeArgs &a, int64_t x, int lane
     for (int e = 0; e < NE; ++e) {
         const int q = lane + 32 * e;
         if (q < a.K) {
-            X.k[e] = dkey(a.key[x * a.K + q]);
-            X.i[e] = a.idx[x * a.K + q];
+            X.k[e] = dkey(a.in_key[x * a.K + q]);
+            X.i[e] = a.in_idx[x * a.K + q];
+            X.old[e] = a.in_flag ? (a.in_flag[x * a.K + q] ? 0 : 1) : 1;
         } else {
             X.k[e] = 0;
             X.i[e] = -1;
+            X.old[e] = 1;
         }
-        X.old[e] = 1;
     }
 }
 
@@ -227,7 +235,7 @@ __device__ __forceinline__ void flush_counts(const MergeArgs &a, int newcount, l
         fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (newcount) atomicAdd((unsigned long long *)&a.cnt[kCntUpdates], (unsigned long long)newcount);
+        if (newcount && a.count) atomicAdd((unsigned long long *)&a.cnt[kCntUpdates], (unsigned long long)newcount);
         if (rescored) atomicAdd((unsigned long long *)&a.cnt[kCntRescored], (unsigned long long)rescored);
         if (fallbacks) atomicAdd((unsigned long long *)&a.cnt[kCntFallback], (unsigned long long)fallbacks);
     }
@@ -703,14 +711,24 @@ static void launch_merge_pair(knnd_handle *h, const MergeArgs &a, int64_t grid, 
 
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag)
 {
+    return launch_merge_from(h, idx, key, nullptr, idx, key, newflag, true);
+}
+
+cudaError_t launch_merge_from(knnd_handle *h, const int32_t *in_idx, const double *in_key, const uint8_t *in_flag,
+                              int32_t *idx, double *key, uint8_t *newflag, bool count)
+{
     MergeArgs a;
     a.n = h->n;
     a.K = h->K;
     a.MP = h->MP;
     a.M2 = (h->m + 1) / 2;
+    a.in_idx = in_idx;
+    a.in_key = in_key;
+    a.in_flag = in_flag;
     a.idx = idx;
     a.key = key;
     a.flag = newflag;
+    a.count = count ? 1 : 0;
     a.cof_off = h->cof_off;
     a.bcnt = h->bcnt;
     a.bent = h->bent;
