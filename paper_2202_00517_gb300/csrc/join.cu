@@ -159,6 +159,13 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
         }
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
         const int64_t nrows = (int64_t)K + (c1 - c0);
+        if (INC) {
+            // no arc of the hub is new: every pair of its tile was met through
+            // arcs of G_{r-2}, in the previous round's pool, and none can change G_r
+            bool any = false;
+            for (int64_t r = lane; r < nrows; r += 32) any |= row_new(a, v, K, c0, r) != 0;
+            if (!__any_sync(0xffffffffu, any)) continue;
+        }
         // the hub's own log row: column v of the co-friend pairs, row slot 32
         for (int i4 = lane; i4 < MP / 4; i4 += 32)
             reinterpret_cast<float4 *>(sX + 32 * S::RS)[i4] =
@@ -461,6 +468,12 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
 
     for (int64_t v = a.h_lo + (int64_t)blockIdx.x * wpb + warp; v < a.h_hi; v += (int64_t)gridDim.x * wpb) {
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
+        if (a.flag) {  // incremental proposals: a hub with no new arc has nothing to propose
+            const int64_t h0 = a.cof_off[v], hn = (int64_t)K + (a.cof_off[v + 1] - h0);
+            bool any = false;
+            for (int64_t r = lane; r < hn; r += 32) any |= row_new(a, v, K, h0, r) != 0;
+            if (!__any_sync(FULL, any)) continue;
+        }
         int cid[CPL], cnew[CPL];
         double cnh[CPL];  // column offsets (reverse KL: negH(y); squared Euclidean: |y|^2)
         double Lc[CPL][MP];

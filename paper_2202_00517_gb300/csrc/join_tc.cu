@@ -176,6 +176,13 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
 
     for (int64_t v = a.h_lo + blockIdx.x; v < a.h_hi; v += gridDim.x) {
         if (!a.iv.live(v)) continue;
+        if (a.flag) {  // incremental proposals: a hub with no new arc has nothing to propose
+            const int64_t h0 = a.cof_off[v], hn = (int64_t)K + (a.cof_off[v + 1] - h0);
+            int any = 0;
+            for (int64_t r = t; r < hn; r += blockDim.x)
+                any |= (r < K ? a.flag[v * K + r] : a.cof_new[h0 + (r - K)]) != 0;
+            if (!__syncthreads_or(any)) continue;
+        }
         // columns: F(v), then v itself (the co-friend column of the rows of F(v))
         for (int j = t; j < N; j += blockDim.x) {
             int id = -1;
