@@ -158,14 +158,17 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
     // incremental proposals read the flags of G_{r-1} (the join runs before the
     // merge overwrites them with those of G_r)
     h->round_flag = (h->prm.incremental && newflag) ? newflag : nullptr;
+    // one instance: the hubs [0, n / den) then the rest; several instances
+    // (batched form): each instance's first n_i / den hubs, then the rest
     const bool split = h->idxA && round >= 1 && round <= kSplitRounds;
-    const int64_t hs = split ? std::max<int64_t>(1, h->n / kSplitDen) : h->n;
+    const bool by_phase = split && h->iv.of;
+    const int64_t hs = !split ? h->n : (by_phase ? h->n : std::max<int64_t>(1, h->n / kSplitDen));
     int t = phase_begin(h, KNND_PHASE_CSR);
     cudaError_t e = launch_reverse_csr(h, idx, key);
     phase_end(h, t, KNND_PHASE_CSR);
     if (e == cudaSuccess) {
         t = phase_begin(h, KNND_PHASE_JOIN);
-        e = launch_join(h, idx, 0, hs);
+        e = launch_join(h, idx, 0, hs, by_phase ? 1 : 0, (int)kSplitDen);
         phase_end(h, t, KNND_PHASE_JOIN);
     }
     if (e == cudaSuccess) {
@@ -180,7 +183,7 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
         phase_end(h, t, KNND_PHASE_CSR);
         if (e == cudaSuccess) {
             t = phase_begin(h, KNND_PHASE_JOIN);
-            e = launch_join(h, idx, hs, h->n);
+            e = by_phase ? launch_join(h, idx, 0, h->n, 2, (int)kSplitDen) : launch_join(h, idx, hs, h->n);
             phase_end(h, t, KNND_PHASE_JOIN);
         }
         if (e == cudaSuccess) {
@@ -460,9 +463,9 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
     if (!s) s = dalloc(h, &h->fb_list, n);
     if (!s) s = dalloc(h, &h->fb_count, 1);
     if (!s) s = dalloc(h, &h->cnt, kCntNum);
-    if (!s && c.ninst == 0) s = dalloc(h, &h->idxA, c.nK);  // split rounds (single instance)
-    if (!s && c.ninst == 0) s = dalloc(h, &h->keyA, c.nK);
-    if (!s && c.ninst == 0) s = dalloc(h, &h->flagA, c.nK);
+    if (!s) s = dalloc(h, &h->idxA, c.nK);  // the split first round's graph copy
+    if (!s) s = dalloc(h, &h->keyA, c.nK);
+    if (!s) s = dalloc(h, &h->flagA, c.nK);
     if (!s && cudaMallocHost((void **)&h->cnt_host, sizeof(int64_t) * kCntNum) != cudaSuccess) s = KNND_ENOMEM;
     if (!s && c.ninst > 0) {
         if (!s) s = dalloc(h, &h->inst_of, n);

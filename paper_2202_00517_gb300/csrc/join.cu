@@ -30,7 +30,8 @@ namespace knnd {
 
 struct JoinArgs {
     int64_t n;
-    int64_t h_lo, h_hi;  // the hubs this launch takes: [h_lo, h_hi)
+    int64_t h_lo, h_hi;  // the hubs this launch takes: [h_lo, h_hi), those of phase `phase` (in_phase)
+    int phase, split_den;
     int K;
     const int32_t *idx;
     const int64_t *cof_off;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
             nc1 = a.cof_off[v + vstep + 1];
         }
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
+        if (!in_phase(a.iv, a.phase, a.split_den, n, v)) continue;
         const int64_t nrows = (int64_t)K + (c1 - c0);
         if (INC) {
             // no arc of the hub is new: every pair of its tile was met through
@@ -468,6 +470,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
 
     for (int64_t v = a.h_lo + (int64_t)blockIdx.x * wpb + warp; v < a.h_hi; v += (int64_t)gridDim.x * wpb) {
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
+        if (!in_phase(a.iv, a.phase, a.split_den, n, v)) continue;
         if (a.flag) {  // incremental proposals: a hub with no new arc has nothing to propose
             const int64_t h0 = a.cof_off[v], hn = (int64_t)K + (a.cof_off[v + 1] - h0);
             bool any = false;
@@ -669,14 +672,16 @@ static cudaError_t run_join_cpl(knnd_handle *h, const JoinArgs &a)
     return run_join<MP, 2>(h, a);
 }
 
-cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi)
+cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase, int split_den)
 {
     if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && h->prm.comparator == KNND_CMP_KL)
-        return launch_join_tc(h, idx, h_lo, h_hi);
+        return launch_join_tc(h, idx, h_lo, h_hi, phase, split_den);
     JoinArgs a;
     a.n = h->n;
     a.h_lo = h_lo;
     a.h_hi = h_hi;
+    a.phase = phase;
+    a.split_den = split_den;
     a.K = h->K;
     a.idx = idx;
     a.cof_off = h->cof_off;

@@ -32,7 +32,8 @@ namespace knnd {
 
 struct TcArgs {
     int64_t n;
-    int64_t h_lo, h_hi;  // the hubs this launch takes: [h_lo, h_hi)
+    int64_t h_lo, h_hi;  // the hubs this launch takes: [h_lo, h_hi), those of phase `phase` (in_phase)
+    int phase, split_den;
     int K;
     const int32_t *idx;
     const int64_t *cof_off;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
 
     for (int64_t v = a.h_lo + blockIdx.x; v < a.h_hi; v += gridDim.x) {
         if (!a.iv.live(v)) continue;
+        if (!in_phase(a.iv, a.phase, a.split_den, n, v)) continue;
         if (a.flag) {  // incremental proposals: a hub with no new arc has nothing to propose
             const int64_t h0 = a.cof_off[v], hn = (int64_t)K + (a.cof_off[v + 1] - h0);
             int any = 0;
@@ -434,12 +436,15 @@ static cudaError_t run_tc_n(knnd_handle *h, const TcArgs &a)
 
 bool tc_supported(int MP, int K) { return MP >= 8 && MP <= 128 && K + 1 <= 80; }
 
-cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi)
+cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase,
+                           int split_den)
 {
     TcArgs a;
     a.n = h->n;
     a.h_lo = h_lo;
     a.h_hi = h_hi;
+    a.phase = phase;
+    a.split_den = split_den;
     a.K = h->K;
     a.idx = idx;
     a.cof_off = h->cof_off;

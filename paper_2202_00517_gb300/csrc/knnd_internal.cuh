@@ -125,6 +125,20 @@ struct InstView {
     __device__ __forceinline__ bool live(int64_t x) const { return !of || active[of[x]] != 0; }
 };
 
+// Hubs of one phase of a split round: phase 0 every hub; 1 the hubs whose
+// index within their instance is below n_i / den; 2 the others.
+__device__ __forceinline__ bool in_phase(const InstView &iv, int phase, int den, int64_t n, int64_t v)
+{
+    if (phase == 0) return true;
+    int64_t local = v, ni = n;
+    if (iv.of) {
+        const int i = iv.of[v];
+        local = v - iv.base[i];
+        ni = iv.n[i];
+    }
+    return (local * den < ni) == (phase == 1);
+}
+
 // Per-row data the mixed join reads with every row it gathers, packed in one
 // 16-byte record (one memory sector): the rejection threshold phi and the
 // start of the row's bucket, K*K*x + (K+1)*cof_off[x].
@@ -264,8 +278,11 @@ cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round);
 cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, double *key, uint8_t *newflag);
 cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key);
 cudaError_t launch_thresholds(knnd_handle *h, const int32_t *idx, const double *key);
-cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi);
-cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi);
+// The join over the hubs [h_lo, h_hi) of phase `phase` (see in_phase, den = split_den).
+cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase = 0,
+                        int split_den = 1);
+cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase,
+                           int split_den);
 double bound_c_bf16x3(int MP);
 bool tc_supported(int MP, int K);
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag);
