@@ -137,7 +137,6 @@ knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
     return s;
 }
 
-// G_{r-1} -> G_r in place; counters kCntUpdates/kCntRescored accumulate.
 // Split first round.  Round 1 proposes nearly its whole pool (the K-th of K
 // random friends is a poor threshold), so it runs in two phases: the hubs
 // [0, n / kSplitDen) propose and their candidates are merged into a copy of the
@@ -151,7 +150,8 @@ knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
 constexpr int32_t kSplitRounds = 1;
 constexpr int64_t kSplitDen = 8;
 
-// loop: a round of the device-driven loop (the FCC sample reads seed and round there).
+// G_{r-1} -> G_r in place; the device counters accumulate.  loop: a round of
+// the device-driven loop (the FCC sample reads seed and round there).
 knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx, double *key, uint8_t *newflag,
                      int64_t *fcc_hits, const LoopState *loop = nullptr)
 {
