@@ -185,8 +185,8 @@ int64_t bytes_per_point(int32_t m, int32_t K, bool mixed, bool incremental)
 {
     const int64_t MP = pad_coords(m);
     const int64_t bucket = (int64_t)K * (2 * K + 1) * (mixed ? 8 : 16);
-    // tables, per-row scalars, buckets, CSR, graph, the split round's graph copy (13 B per arc)
-    return MP * 24 + 96 + bucket + (int64_t)K * (4 + 4 + 8 + 13 + (incremental ? 2 : 0));
+    // tables, per-row scalars, buckets, CSR and arc slots, graph, the split round's graph copy (13 B per arc)
+    return MP * 24 + 96 + bucket + (int64_t)K * (4 + 4 + 4 + 8 + 13 + (incremental ? 2 : 0));
 }
 
 // One sub-batch: all its instances from points to graphs.

@@ -52,7 +52,8 @@ __device__ __forceinline__ void row_thresholds(int64_t x, double t, int32_t v, d
 
 // One thread per arc e = x*K + t (x -> idx[e]).
 __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *__restrict__ key, int64_t n, int K,
-                                 int32_t *__restrict__ deg, double *__restrict__ tau, int32_t *__restrict__ idxK,
+                                 int32_t *__restrict__ deg, int32_t *__restrict__ slot, double *__restrict__ tau,
+                                 int32_t *__restrict__ idxK,
                                  const double *__restrict__ negH, const double *__restrict__ nx,
                                  const unsigned long long *__restrict__ smax_bits, InstView iv, double bound_c,
                                  int cmp,
@@ -64,7 +65,7 @@ __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *
     if (v < 0 || v >= n) {
         atomicOr(err, kErrIndex);
     } else {
-        atomicAdd(&deg[v], 1);
+        slot[e] = atomicAdd(&deg[v], 1);  // the arc's position in coF(v)
     }
     if (e % K == K - 1)
         row_thresholds(e / K, key[e], v, tau, idxK, negH, nx, smax_bits, iv, bound_c, cmp, meta, Ex);
@@ -165,20 +166,21 @@ __global__ void scan_apply_kernel(const int32_t *__restrict__ deg, int64_t n, co
     }
 }
 
-// One thread per arc x -> v: append x to coF(v).  The order inside a list is
-// not fixed; every consumer treats the list as a set.
-// With flag (incremental proposals), the arc's new-flag goes with it.
-__global__ void csr_fill_kernel(const int32_t *__restrict__ idx, int64_t n, int K, const int64_t *__restrict__ off,
-                                int32_t *__restrict__ cursor, int32_t *__restrict__ cof,
+// One thread per arc x -> v: x goes to coF(v) at the position the count pass
+// drew for the arc.  The order inside a list is not fixed; every consumer
+// treats the list as a set.  With flag (incremental proposals), the arc's
+// new-flag goes with it.
+__global__ void csr_fill_kernel(const int32_t *__restrict__ idx, const int32_t *__restrict__ slot, int64_t n, int K,
+                                const int64_t *__restrict__ off, int32_t *__restrict__ cof,
                                 const uint8_t *__restrict__ flag, uint8_t *__restrict__ cof_new)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * K) return;
     const int32_t v = idx[e];
     if (v < 0 || v >= n) return;
-    const int32_t p = atomicAdd(&cursor[v], 1);
-    cof[off[v] + p] = (int32_t)(e / K);
-    if (flag) cof_new[off[v] + p] = flag[e];
+    const int64_t q = off[v] + slot[e];
+    cof[q] = (int32_t)(e / K);
+    if (flag) cof_new[q] = flag[e];
 }
 
 cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key)
@@ -190,7 +192,8 @@ cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double 
     const unsigned eblocks = (unsigned)((E + threads - 1) / threads);
     cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
     const bool mixed = h->prec != KNND_PREC_FP64;
-    csr_count_kernel<<<eblocks, threads, 0, h->stream>>>(idx, key, n, K, h->deg, h->tau, h->idxK, h->negH, h->nx,
+    csr_count_kernel<<<eblocks, threads, 0, h->stream>>>(idx, key, n, K, h->deg, h->slot, h->tau, h->idxK, h->negH,
+                                                         h->nx,
                                                          h->smax_bits, h->iv, h->bound_c, h->prm.comparator,
                                                          mixed ? h->meta : nullptr,
                                                          h->Ex, h->err);
@@ -199,8 +202,7 @@ cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double 
     scan_sums_kernel<<<1, kScanThreads, 0, h->stream>>>(h->scan_tmp, ntiles, h->cof_off, n);
     scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp, h->cof_off,
                                                                         mixed ? h->meta : nullptr, K);
-    cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
-    csr_fill_kernel<<<eblocks, threads, 0, h->stream>>>(idx, n, K, h->cof_off, h->deg, h->cof, h->round_flag,
+    csr_fill_kernel<<<eblocks, threads, 0, h->stream>>>(idx, h->slot, n, K, h->cof_off, h->cof, h->round_flag,
                                                         h->cof_new);
     h->launches += 5;
     return cudaGetLastError();

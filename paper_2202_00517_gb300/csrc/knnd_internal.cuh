@@ -195,7 +195,8 @@ struct knnd_handle {
     unsigned long long *smax_bits;
     int32_t *err;                   // device error word
     // reverse CSR
-    int32_t *deg;     // n: in-degree, then fill cursor
+    int32_t *deg;     // n: in-degree
+    int32_t *slot;    // n*K: each arc's position in its co-friend list
     int64_t *cof_off; // n+1
     int32_t *cof;     // n*K
     // incremental proposals (params.incremental): the new-flag of the arc x -> v
