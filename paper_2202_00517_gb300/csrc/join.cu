@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
         if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
         if (!in_phase(a.iv, a.phase, a.split_den, n, v)) continue;
         const int64_t nrows = (int64_t)K + (c1 - c0);
-        if (INC) {
-            // no arc of the hub is new: every pair of its tile was met through
-            // arcs of G_{r-2}, in the previous round's pool, and none can change G_r
+        // INC: no arc of the hub is new, so every pair of its tile was met through
+        // arcs of G_{r-2}, in the previous round's pool, and none can change G_r
+        // (the fast path reads the first 32 flags with the ids)
+        if (INC && !fast) {
             bool any = false;
             for (int64_t r = lane; r < nrows; r += 32) any |= row_new(a, v, K, c0, r) != 0;
             if (!__any_sync(0xffffffffu, any)) continue;
@@ -182,6 +183,11 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                     atomicOr(a.err, kErrIndex);
                     rid0 = -1;
                 }
+            }
+            if (INC) {
+                bool any = lane < nrows && rnew0;
+                for (int64_t r = 32 + lane; r < nrows; r += 32) any |= row_new(a, v, K, c0, r) != 0;
+                if (!__any_sync(0xffffffffu, any)) continue;
             }
             if (lane < K) {
                 sCid[lane] = rid0;
