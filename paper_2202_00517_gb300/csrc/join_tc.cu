@@ -131,8 +131,10 @@ __device__ __forceinline__ bool mbar_wait_ns(uint32_t bar, uint32_t parity, unsi
     }
 }
 
+// 64 registers (eight CTAs per SM) while the accumulator row is at most 32 wide;
+// wider rows keep theirs in registers at 128
 template <int MP, int KD, int N>
-__global__ void __launch_bounds__(128) join_tc_kernel(TcArgs a)
+__global__ void __launch_bounds__(128, N <= 32 ? 8 : 4) join_tc_kernel(TcArgs a)
 {
     using Lay = TcLayout<KD, N>;
     extern __shared__ __align__(1024) unsigned char smem[];
