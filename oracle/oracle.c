@@ -162,15 +162,24 @@ void orc_logs(const double *pts, int64_t n, int m, double *L, double *negH)
  *   0  D(x||y) = key(x, y), the paper's (Sec. 2.2, Sec. 4.4);
  *   1  D(y||x) = key(y, x), the KL divergence the other way round;
  *   2  |x - y|^2 = (|x|^2 - 2 <x, y>) + |y|^2, a symmetric metric comparator,
- *      |x|^2 and <x, y> sequential fma chains from 0 (2 <x, y> is exact). */
+ *      |x|^2 and <x, y> sequential fma chains from 0 (2 <x, y> is exact);
+ *   3  0 - <x, y>: the larger the inner product, the closer (maximum inner
+ *      product neighbours), <x, y> a sequential fma chain from 0. */
 static int orc_cmp = 0;
 
-void orc_set_comparator(int32_t c) { orc_cmp = (c == 1 || c == 2) ? c : 0; }
+void orc_set_comparator(int32_t c) { orc_cmp = (c >= 1 && c <= 3) ? c : 0; }
 
 /* Per-point tables of the comparator: KL forms L = log(x), off = negH(x);
- * squared Euclidean L unused, off = |x|^2. */
+ * squared Euclidean L unused, off = |x|^2; inner product L = x, off = 0. */
 static void orc_tables(const double *pts, int64_t n, int m, double *L, double *off)
 {
+    if (orc_cmp == 3) {
+        for (int64_t y = 0; y < n; ++y) {
+            for (int i = 0; i < m; ++i) L[y * m + i] = pts[y * m + i];
+            off[y] = 0.0;
+        }
+        return;
+    }
     if (orc_cmp != 2) {
         orc_logs(pts, n, m, L, off);
         return;
@@ -184,7 +193,8 @@ static void orc_tables(const double *pts, int64_t n, int m, double *L, double *o
 
 /* key(x, y) for the comparator: KL negH(x) - sum_i x_i * log(y_i) (the inner
  * sum an fma chain from 0 over i = 0..m-1), the roles swapped for 1;
- * squared Euclidean (off(x) - 2 sum_i x_i y_i) + off(y). */
+ * squared Euclidean (off(x) - 2 sum_i x_i y_i) + off(y); inner product
+ * 0 - sum_i x_i y_i (the KL form's chain with L = x and off = 0). */
 static double orc_key_from_tables(const double *pts, const double *L, const double *off,
                                   int m, int64_t x, int64_t y)
 {

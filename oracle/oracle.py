@@ -85,12 +85,13 @@ def _load():
 _dir_lock = threading.Lock()
 
 
-COMPARATORS = {"kl": 0, "kl_reverse": 1, "sqeuclidean": 2}
+COMPARATORS = {"kl": 0, "kl_reverse": 1, "sqeuclidean": 2, "inner": 3}
 
 
 class _comparator:
     """Comparator for the calls inside: "kl" ranks y for x by D(x||y) (the
-    paper's), "kl_reverse" by D(y||x), "sqeuclidean" by |x - y|^2."""
+    paper's), "kl_reverse" by D(y||x), "sqeuclidean" by |x - y|^2, "inner" by
+    -<x, y> (the largest inner products first)."""
 
     def __init__(self, comparator):
         self.c = COMPARATORS[comparator]
@@ -156,7 +157,7 @@ def logs(points):
 def keys_pairs(points, xs, ys, comparator: str = "kl") -> np.ndarray:
     """Canonical FP64 key of each pair under the comparator: "kl" negH(x) - <x, log y>,
     "kl_reverse" the same with the roles swapped (D(y||x)), "sqeuclidean"
-    (|x|^2 - 2 <x, y>) + |y|^2."""
+    (|x|^2 - 2 <x, y>) + |y|^2, "inner" 0 - <x, y>."""
     p = _pts(points)
     n, m = p.shape
     xs = np.ascontiguousarray(xs, dtype=np.int32)

@@ -22,6 +22,8 @@ def _scipy_keys(p, x, ys, comparator="kl"):
         return rel_entr(p[ys], p[x][None, :]).sum(1)
     if comparator == "sqeuclidean":
         return cdist(p[x][None, :], p[ys], "sqeuclidean")[0]
+    if comparator == "inner":
+        return -(p[ys] @ p[x])
     return rel_entr(p[x][None, :], p[ys]).sum(1)
 
 
@@ -82,11 +84,11 @@ def _python_pool(idx, x):
     return pool
 
 
-@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean"])
+@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean", "inner"])
 def test_round_equals_independent_pool_topk(comparator):
     n, m, K = 80, 4, 5
     p = dirichlet_points(n, m, 21, np.float64)
-    if comparator == "sqeuclidean":  # any finite coordinates
+    if comparator in ("sqeuclidean", "inner"):  # any finite coordinates
         p = np.random.default_rng(21).standard_normal((n, m))
     idx0, _ = oracle.init_graph(p, K, 21, comparator=comparator)
     pools = oracle.pools(idx0)
@@ -159,7 +161,7 @@ def test_round_row_range():
 
 
 # ---------------------------------------------------------------- brute force
-@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean"])
+@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean", "inner"])
 def test_bruteforce_matches_full_matrix(comparator):
     n, m, K = 300, 6, 9
     p = dirichlet_points(n, m, 13, np.float64)
@@ -169,6 +171,8 @@ def test_bruteforce_matches_full_matrix(comparator):
         D = D.T.copy()  # row x: D(y||x)
     elif comparator == "sqeuclidean":
         D = cdist(p, p, "sqeuclidean")
+    elif comparator == "inner":
+        D = -(p @ p.T)
     np.fill_diagonal(D, np.inf)
     for x in range(n):
         order = np.lexsort((np.arange(n), D[x]))[:K]

@@ -117,3 +117,23 @@ def test_squared_euclidean_matches_numpy():
     assert np.all(np.abs(k - ref) <= 1e-14 * scale)
     # symmetric, up to the last rounding of the two orders of the sum
     assert np.allclose(k, oracle.keys_pairs(p, ys, xs, comparator="sqeuclidean"), rtol=0, atol=1e-14 * scale.max())
+
+
+def test_inner_product_matches_numpy():
+    # maximum inner product neighbours: key 0 - <x, y>, any finite coordinates
+    p = np.random.default_rng(5).standard_normal((300, 13)) * 2.0
+    rng = np.random.default_rng(6)
+    xs = rng.integers(0, 300, 3000)
+    ys = rng.integers(0, 300, 3000)
+    k = oracle.keys_pairs(p, xs, ys, comparator="inner")
+    ref = -(p[xs] * p[ys]).sum(1)
+    scale = (np.abs(p[xs]) * np.abs(p[ys])).sum(1)
+    assert np.all(np.abs(k - ref) <= 1e-14 * scale)
+    # the chain is the KL form's with L = x and negH = 0: exact sign of an empty sum
+    z = np.zeros((2, 3))
+    kz = oracle.keys_pairs(z, [0], [1], comparator="inner")[0]
+    assert kz == 0.0 and not np.signbit(kz)  # 0 - (+0) = +0
+    # not a metric: a point need not be its own best match
+    q = np.array([[1.0, 0.0], [2.0, 0.0], [0.0, 1.0]])
+    kk = oracle.keys_pairs(q, [0, 0], [1, 0], comparator="inner")
+    assert kk[0] < kk[1]
