@@ -285,6 +285,7 @@ def gpu_single(args, name, rank, world, local, barrier):
         other = "bf16x3" if args.form == "mixed" else "mixed"
         for vname, prec, kw in ((other, other, {}), ("kl_reverse", args.form, {"comparator": "kl_reverse"}),
                                 ("sqeuclidean", args.form, {"comparator": "sqeuclidean"}),
+                                ("inner", args.form, {"comparator": "inner"}),
                                 ("stop_delta_0.001", args.form, {"stop_delta": 0.001})):
             variants[vname] = run_form(prec, vsteps, 1, **kw)
 

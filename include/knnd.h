@@ -1,8 +1,8 @@
 /*
  * knnd.h -- C ABI of the GB300 (sm_103a) K-nearest-neighbour descent library
  * for the Kullback-Leibler comparator on points of the probability simplex
- * (and, as variants, the reverse KL divergence and the squared Euclidean
- * distance: knnd_params.comparator).
+ * (and, as variants, the reverse KL divergence, the squared Euclidean
+ * distance and the inner product: knnd_params.comparator).
  *
  * Method: Baron & Darling, "Empirical complexity of comparator-based nearest
  * neighbor descent", arXiv:2202.00517.
@@ -29,7 +29,8 @@
  *     (key[x][t] = D(x || idx[x][t]) evaluated in FP64 as
  *     sum_i x_i log x_i - sum_i x_i log y_i, both sums fma chains from 0;
  *     KNND_CMP_KL_REVERSE: D(idx[x][t] || x), the same with the roles
- *     swapped; KNND_CMP_SQEUCLIDEAN: (|x|^2 - 2 <x, y>) + |y|^2), newflag is n x K uint8 (1 when
+ *     swapped; KNND_CMP_SQEUCLIDEAN: (|x|^2 - 2 <x, y>) + |y|^2; KNND_CMP_INNER: 0 - <x, y>),
+ *     newflag is n x K uint8 (1 when
  *     the entry was not in the row before the call).  Each row is sorted by
  *     (key ascending, idx ascending).  Caller-owned device buffers.
  *   - Work is enqueued on the handle's stream (a cudaStream_t passed as
@@ -113,6 +114,8 @@ typedef struct {
 #define KNND_CMP_KL_REVERSE 1  /* D(y || x): the asymmetric divergence the other way round; coordinates > 0 */
 #define KNND_CMP_SQEUCLIDEAN 2 /* |x - y|^2 = (|x|^2 - 2 <x, y>) + |y|^2 (fma chains): a symmetric metric
                                   comparator; any finite coordinates */
+#define KNND_CMP_INNER 3       /* 0 - <x, y> (fma chain): maximum inner product neighbours, the largest
+                                  inner products first (not a metric); any finite coordinates */
 
 /* Why knnd_build stopped. */
 #define KNND_STOP_FCC 1        /* clustering hits did not increase (Sec. 3.3 (iv)) */

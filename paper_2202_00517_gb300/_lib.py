@@ -36,6 +36,7 @@ KNND_STOP_DELTA = 4
 KNND_CMP_KL = 0
 KNND_CMP_KL_REVERSE = 1
 KNND_CMP_SQEUCLIDEAN = 2
+KNND_CMP_INNER = 3
 KNND_LOOP_AUTO = 0
 KNND_LOOP_HOST = 1
 KNND_LOOP_GRAPH = 2

@@ -17,7 +17,8 @@ from ._lib import check
 _PREC = {"fp64": _lib.KNND_PREC_FP64, "mixed": _lib.KNND_PREC_MIXED_FP32,
          "mixed_fp32": _lib.KNND_PREC_MIXED_FP32, "bf16x3": _lib.KNND_PREC_MIXED_BF16X3,
          "auto": _lib.KNND_PREC_AUTO}
-_CMP = {"kl": _lib.KNND_CMP_KL, "kl_reverse": _lib.KNND_CMP_KL_REVERSE, "sqeuclidean": _lib.KNND_CMP_SQEUCLIDEAN}
+_CMP = {"kl": _lib.KNND_CMP_KL, "kl_reverse": _lib.KNND_CMP_KL_REVERSE, "sqeuclidean": _lib.KNND_CMP_SQEUCLIDEAN,
+        "inner": _lib.KNND_CMP_INNER}
 _LOOP = {"auto": _lib.KNND_LOOP_AUTO, "host": _lib.KNND_LOOP_HOST, "graph": _lib.KNND_LOOP_GRAPH}
 _DTYPE = {"f32": _lib.KNND_F32, "f64": _lib.KNND_F64, torch.float32: _lib.KNND_F32,
           torch.float64: _lib.KNND_F64}

@@ -552,7 +552,7 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
     if (prm.incremental != 0 && prm.incremental != 1) return KNND_EINVAL;
     if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
-    if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_SQEUCLIDEAN) return KNND_EINVAL;
+    if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_INNER) return KNND_EINVAL;
     if (prm.debug < 0 || prm.debug > 2) return KNND_EINVAL;
     if (prm.loop < KNND_LOOP_AUTO || prm.loop > KNND_LOOP_GRAPH) return KNND_EINVAL;
     if (prm.loop == KNND_LOOP_GRAPH && prm.timing) return KNND_EINVAL;  // event nodes cannot sit in the loop body

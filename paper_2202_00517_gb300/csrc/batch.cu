@@ -315,7 +315,7 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
     if (prm.fcc_samples < 1 || prm.max_rounds < 1 || prm.max_rounds > KNND_MAX_ROUNDS) return KNND_EINVAL;
     if (prm.incremental != 0 && prm.incremental != 1) return KNND_EINVAL;
     if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
-    if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_SQEUCLIDEAN) return KNND_EINVAL;
+    if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_INNER) return KNND_EINVAL;
     if (prm.loop < KNND_LOOP_AUTO || prm.loop > KNND_LOOP_GRAPH) return KNND_EINVAL;
     if (prm.timing) prm.timing = 0;  // phase timing is a single-instance feature
     const bool mixed = precision != KNND_PREC_FP64;

@@ -17,7 +17,7 @@ __device__ __forceinline__ void row_thresholds(int64_t x, double t, int32_t v, d
 {
     tau[x] = t;
     idxK[x] = v;
-    if (meta && cmp == KNND_CMP_KL) {
+    if (meta && (cmp == KNND_CMP_KL || cmp == KNND_CMP_INNER)) {  // inner: negH = 0, L = coordinates
         // |fp32 dot - fp64 dot| <= c_m * sum_i |x_i||log y_i| <= c_m * nx(x) * max|log|.
         // margin covers the FP64 roundings of the key and threshold arithmetic.
         const double smax = __longlong_as_double((long long)smax_bits[3 * iv.at(x)]);

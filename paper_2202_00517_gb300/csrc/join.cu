@@ -75,6 +75,13 @@ __device__ __forceinline__ int row_new(const JoinArgs &a, int64_t v, int K, int6
 
 __device__ __forceinline__ bool valid_id(int64_t v, int64_t n) { return v >= 0 && v < n; }
 
+// Comparators whose key has a per-column offset co(y) (reverse KL, squared
+// Euclidean); KL and inner product have none (key = ro(x) - <R(x), C(y)>).
+__host__ __device__ __forceinline__ bool has_col_offset(int cmp)
+{
+    return cmp == KNND_CMP_KL_REVERSE || cmp == KNND_CMP_SQEUCLIDEAN;
+}
+
 // ------------------------------------------------------------------ mixed
 // Lane (g, p): column pair p (columns 2p, 2p+1; their FP32 log rows live in
 // registers) of row group g; a pass scores two rows per group, 2 x G rows in
@@ -500,7 +507,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                 }
             }
             cid[c] = id;
-            cnh[c] = (a.cmp != KNND_CMP_KL && id >= 0) ? a.negH[id] : 0.0;
+            cnh[c] = (has_col_offset(a.cmp) && id >= 0) ? a.negH[id] : 0.0;
             const double2 *lr = reinterpret_cast<const double2 *>(a.L64 + (int64_t)(id < 0 ? 0 : id) * MP);
 #pragma unroll
             for (int i2 = 0; i2 < MP / 2; ++i2) {
@@ -569,7 +576,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                 }
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
-                    const double k = a.cmp == KNND_CMP_KL           ? rnh - acc[c]
+                    const double k = !has_col_offset(a.cmp)         ? rnh - acc[c]
                                      : a.cmp == KNND_CMP_KL_REVERSE ? cnh[c] - acc[c]
                                                                     : (rnh - 2.0 * acc[c]) + cnh[c];
                     const bool pass = rrid >= 0 && cid[c] >= 0 && cid[c] != rrid && (rrnew || cnew[c]) &&
@@ -591,7 +598,7 @@ __global__ void __launch_bounds__(128) join_fp64_kernel(JoinArgs a)
                     acc = __fma_rn(xv.x, lw.x, acc);
                     acc = __fma_rn(xv.y, lw.y, acc);
                 }
-                cfk = a.cmp == KNND_CMP_KL           ? nh - acc
+                cfk = !has_col_offset(a.cmp)         ? nh - acc
                       : a.cmp == KNND_CMP_KL_REVERSE ? a.negH[v] - acc
                                                      : (nh - 2.0 * acc) + a.negH[v];
                 cfpass = rnew && lex_less(cfk, (int)v, tk, ik);
@@ -657,7 +664,7 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         using S = MixedSmem<MP>;
         const int threads = 128;
         const size_t smem = (size_t)S::warp_bytes(h->K) * (threads / 32);
-        const bool col = a.cmp != KNND_CMP_KL;
+        const bool col = has_col_offset(a.cmp);
         auto kern = col ? (a.flag ? join_mixed_kernel<MP, true, true> : join_mixed_kernel<MP, false, true>)
                         : (a.flag ? join_mixed_kernel<MP, true, false> : join_mixed_kernel<MP, false, false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

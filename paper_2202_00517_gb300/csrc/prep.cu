@@ -16,11 +16,13 @@ namespace knnd {
 // ---------------------------------------------------------------------------
 // Points: pts + x * ld, or (several instances) the row x - base[i] of
 // instance i = iv.of[x] at ptrs[i] with row stride lds[i].
-// Squared Euclidean comparator (sqe): L is a copy of the coordinates and negH
-// holds |x|^2 (fma chain from 0); coordinates need only be finite.
+// mode 0: the KL comparators (L = log x, negH = sum x log x).  Comparators on the
+// coordinates themselves (mode 1: squared Euclidean; mode 2: inner product): L is
+// a copy of the coordinates and negH holds |x|^2 (fma chain from 0) for the
+// first, 0 for the second; coordinates need only be finite.
 template <typename T>
 __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, const void *const *ptrs,
-                                  const int64_t *lds, InstView iv, int sqe, int64_t n, int m, int MP,
+                                  const int64_t *lds, InstView iv, int mode, int64_t n, int m, int MP,
                                   double *__restrict__ X64, double *__restrict__ L64, float *__restrict__ X32,
                                   float *__restrict__ L32, double *__restrict__ negH, double *__restrict__ nx,
                                   unsigned long long *smax_bits, int32_t *err)
@@ -41,12 +43,12 @@ __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, const v
             double v = 0.0, l = 0.0;
             if (i < m) {
                 v = (double)row[i];
-                if (sqe ? !(fabs(v) <= DBL_MAX) : (!(v > 0.0) || !(v <= DBL_MAX))) {
+                if (mode ? !(fabs(v) <= DBL_MAX) : (!(v > 0.0) || !(v <= DBL_MAX))) {
                     bad = true;
                     v = 1.0;  // keep the tables finite; the call reports EDOMAIN
                 }
-                l = sqe ? v : log(v);
-                acc = __fma_rn(v, l, acc);
+                l = mode ? v : log(v);
+                if (mode != 2) acc = __fma_rn(v, l, acc);
                 s += fabs(v);
                 lmax = fmax(lmax, fabs(l));
             }
@@ -91,6 +93,12 @@ __global__ void precompute_kernel(const T *__restrict__ pts, int64_t ld, const v
     }
 }
 
+// 0: log tables (the KL comparators); 1: squared Euclidean; 2: inner product
+static int coord_mode(int cmp)
+{
+    return cmp == KNND_CMP_SQEUCLIDEAN ? 1 : (cmp == KNND_CMP_INNER ? 2 : 0);
+}
+
 cudaError_t launch_precompute(knnd_handle *h, const void *points, int64_t ld)
 {
     return launch_precompute_from(h, points, ld, nullptr, nullptr);
@@ -104,12 +112,12 @@ cudaError_t launch_precompute_from(knnd_handle *h, const void *points, int64_t l
     cudaMemsetAsync(h->smax_bits, 0, sizeof(unsigned long long) * 3 * (h->ninst > 0 ? h->ninst : 1), h->stream);
     if (h->dtype == KNND_F32)
         precompute_kernel<float><<<(unsigned)blocks, threads, 0, h->stream>>>(
-            (const float *)points, ld, ptrs, lds, h->iv, h->prm.comparator == KNND_CMP_SQEUCLIDEAN, h->n, h->m, h->MP,
+            (const float *)points, ld, ptrs, lds, h->iv, coord_mode(h->prm.comparator), h->n, h->m, h->MP,
             h->X64, h->L64, h->X32, h->L32,
             h->negH, h->nx, h->smax_bits, h->err);
     else
         precompute_kernel<double><<<(unsigned)blocks, threads, 0, h->stream>>>(
-            (const double *)points, ld, ptrs, lds, h->iv, h->prm.comparator == KNND_CMP_SQEUCLIDEAN, h->n, h->m, h->MP,
+            (const double *)points, ld, ptrs, lds, h->iv, coord_mode(h->prm.comparator), h->n, h->m, h->MP,
             h->X64, h->L64, h->X32, h->L32,
             h->negH, h->nx, h->smax_bits, h->err);
     h->launches += 1;
@@ -134,7 +142,8 @@ __device__ __forceinline__ double dot_fp64(const double *__restrict__ X64, const
 
 // The comparator's canonical FP64 key: KL negH(x) - <x, log y>; reverse KL the
 // same with the roles swapped; squared Euclidean (|x|^2 - 2 <x, y>) + |y|^2 (L64
-// then holds the coordinates and negH the squared norms).
+// then holds the coordinates and negH the squared norms); inner product the KL
+// form with L64 the coordinates and negH = 0, i.e. 0 - <x, y>.
 __device__ __forceinline__ double key_cmp(int cmp, const double *__restrict__ X64, const double *__restrict__ L64,
                                           const double *__restrict__ negH, int MP, int64_t x, int64_t y)
 {

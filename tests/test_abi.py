@@ -72,7 +72,7 @@ def test_create_rejects_bad_params(lib):
     for prm in (_lib.knnd_params(0, 10, 1, 0, 0, 1), _lib.knnd_params(100, 0, 1, 0, 0, 1),
                 _lib.knnd_params(100, 65, 1, 0, 0, 1), _lib.knnd_params(100, 10, 1, 0, 0, 2),
                 _lib.knnd_params(100, 10, 1, 0, 0, 0, -0.5), _lib.knnd_params(100, 10, 1, 0, 0, 0, 2.0),
-                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 3),
+                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 4),             # no such comparator
                 _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 3),         # no such loop
                 _lib.knnd_params(100, 10, 1, 0, 1, 0, 0.0, 0, _lib.KNND_LOOP_GRAPH)):  # graph loop with timing
         assert lib.knnd_create(ctypes.byref(h), 1000, 6, 10, 0, 1, ctypes.byref(prm), None) == _lib.KNND_EINVAL

@@ -126,3 +126,19 @@ def test_batched_sqeuclidean_equals_separate_builds():
         h.close()
         assert res[i]["rounds"] == ref["rounds"] and res[i]["updates"] == ref["updates"], i
         assert torch.equal(res[i]["idx"], ref["idx"]) and torch.equal(res[i]["key"], ref["key"]), i
+
+
+def test_batched_inner_product_equals_separate_builds():
+    import paper_2202_00517_gb300 as knnd
+    rng = np.random.default_rng(51)
+    shapes = [(400, 6, 8), (900, 11, 16), (1500, 6, 8)]
+    pts = [torch.from_numpy((rng.standard_normal((n, m)) * 2.0).astype(np.float32)).cuda() for n, m, _ in shapes]
+    Ks = [k for _, _, k in shapes]
+    seeds = [61, 62, 63]
+    res = knnd.build_batched(pts, Ks, seeds, fcc_samples=700, comparator="inner")
+    for (n, m, K), p, sd, r in zip(shapes, pts, seeds, res):
+        h = knnd.Handle(n, m, K, dtype="f32", fcc_samples=700, comparator="inner")
+        out = h.build(p, sd)
+        h.close()
+        assert out["rounds"] == r["rounds"] and out["updates"] == r["updates"]
+        assert torch.equal(out["idx"], r["idx"]) and torch.equal(out["key"], r["key"])

@@ -55,7 +55,7 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "bf16x3"])
-@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean"])
+@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean", "inner"])
 def test_graph_loop_equals_host_loop(knnd, prec, comparator):
     pts = _dev(dirichlet_points(20_000, 21, 3, np.float32))
     a, b = _both(knnd, pts, 20, 3, precision=prec, comparator=comparator)

@@ -331,6 +331,36 @@ def test_sqeuclidean_domain(knnd):
     hk.close()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,m,K,dtype,gauss", [(2000, 6, 10, "f64", True), (1500, 21, 20, "f32", True),
+                                                 (800, 65, 32, "f32", False), (1000, 40, 40, "f64", True)])
+def test_inner_product_lockstep(knnd, prec, n, m, K, dtype, gauss):
+    # maximum inner product neighbours, key 0 - <x, y>: every round against the oracle's
+    npdt = np.float32 if dtype == "f32" else np.float64
+    pts = _gauss(n, m, 43, npdt) if gauss else dirichlet_points(n, m, 43, npdt)
+    assert _lockstep(knnd, pts, K, 43, prec, rounds=3, dtype=dtype, S=500, comparator="inner") <= max(2, n // 500)
+
+
+def test_inner_product_build(knnd):
+    n, m, K, seed, S = 3000, 9, 12, 47, 2000
+    pts = _gauss(n, m, seed)
+    ref = oracle.build(pts, K, seed, S=S, comparator="inner")
+    outs = {}
+    for prec in PRECS:
+        h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="inner")
+        outs[prec] = h.build(_dev(pts), seed)
+        h.close()
+    for prec, out in outs.items():
+        assert out["rounds"] == ref["rounds"] and out["updates"] == list(ref["updates"]), prec
+        assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"]), prec
+        assert torch.equal(out["key"], outs["fp64"]["key"]), prec
+    # the keys are -<x, y> (numpy, to the chain's rounding)
+    idx = outs["mixed"]["idx"].cpu().numpy()
+    key = outs["mixed"]["key"].cpu().numpy()
+    ref_k = -(pts[:, None, :] * pts[idx]).sum(-1)
+    assert np.allclose(key, ref_k, rtol=0, atol=1e-12 * np.abs(pts).sum(1).max() ** 2)
+
+
 def test_bounded_wait_timeout_is_reported(knnd):
     # debug = 2: the tensor-core join's first tile waits on a barrier that no MMA
     # signals; the wait gives up after about a second, the call reports ETIMEOUT,
