@@ -46,6 +46,7 @@ void drop_loop_graph(knnd_handle *h);
 void free_all(knnd_handle *h)
 {
     void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg, h->slot,
+                    h->heavy_items, h->heavy_nitems,
                     h->cof_off, h->cof, h->cof_new, h->flag_tmp, h->scan_tmp, h->tau, h->idxK, h->meta, h->Ex, h->bcnt, h->bkey,
                     h->bent, h->fb_list, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev, h->idxA, h->keyA,
                     h->flagA,
@@ -449,6 +450,8 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
     if (!s) s = dalloc(h, &h->err, 1);
     if (!s) s = dalloc(h, &h->deg, n);
     if (!s) s = dalloc(h, &h->slot, c.nK);
+    if (!s) s = dalloc(h, &h->heavy_items, c.nK / 64 + 16);
+    if (!s) s = dalloc(h, &h->heavy_nitems, 1);
     if (!s) s = dalloc(h, &h->cof_off, n + 1);
     if (!s) s = dalloc(h, &h->cof, c.nK);
     if (!s && prm.incremental) s = dalloc(h, &h->cof_new, c.nK);

@@ -32,6 +32,11 @@ struct JoinArgs {
     int64_t n;
     int64_t h_lo, h_hi;  // the hubs this launch takes: [h_lo, h_hi), those of phase `phase` (in_phase)
     int phase, split_den;
+    // heavy hubs (more than kHeavyRows rows): the main pass skips them and a second
+    // pass spreads their rows over the grid as items (hub, group of kItemRows rows)
+    const int2 *items;        // NULL: no heavy pass
+    const int32_t *nitems;
+    int heavy_pass;           // 1: this launch runs the items
     int K;
     const int32_t *idx;
     const int64_t *cof_off;
@@ -82,6 +87,25 @@ __host__ __device__ __forceinline__ bool has_col_offset(int cmp)
     return cmp == KNND_CMP_KL_REVERSE || cmp == KNND_CMP_SQEUCLIDEAN;
 }
 
+// ------------------------------------------------------------------ heavy hubs
+// A hub's rows are F(v) and coF(v): K + indeg(v).  Skewed graphs (the inner
+// product's, whose best matches are the few points of largest norm) give some
+// hubs tens of thousands of rows, which one warp would take alone.
+constexpr int kHeavyRows = 1024;
+constexpr int kItemRows = 256;
+
+// Items of the heavy pass, one thread per hub of the launch's range.
+__global__ void heavy_items_kernel(JoinArgs a, int2 *items, int32_t *nitems)
+{
+    const int64_t v = a.h_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.h_hi || !a.iv.live(v) || !in_phase(a.iv, a.phase, a.split_den, a.n, v)) return;
+    const int64_t nrows = (int64_t)a.K + (a.cof_off[v + 1] - a.cof_off[v]);
+    if (nrows <= kHeavyRows) return;
+    const int cnt = (int)((nrows + kItemRows - 1) / kItemRows);
+    const int b = atomicAdd(nitems, cnt);
+    for (int k = 0; k < cnt; ++k) items[b + k] = make_int2((int)v, k);
+}
+
 // ------------------------------------------------------------------ mixed
 // Lane (g, p): column pair p (columns 2p, 2p+1; their FP32 log rows live in
 // registers) of row group g; a pass scores two rows per group, 2 x G rows in
@@ -120,7 +144,9 @@ __host__ __device__ constexpr int mixed_min_blocks(int MP) {
 // default form carries none of its state.
 // COL: the comparator has a column offset (reverse KL, squared Euclidean): the
 // filter threshold and the entry take RD(co(y)/s) of each column.
-template <int MP, bool INC, bool COL>
+// PASS: 0 every hub of the launch; 1 the same, the heavy hubs left to pass 2;
+// 2 the heavy pass (items instead of hubs; see heavy_items_kernel).
+template <int MP, bool INC, bool COL, int PASS>
 __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(JoinArgs a)
 {
     using S = MixedSmem<MP>;
@@ -150,30 +176,48 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
     // rows in a second, all in flight together; the columns are staged in the dot
     // buffer (stride CS) until each lane has read its two.  cof_off is read one
     // hub ahead.
-    const bool fast = MP <= 32 && K <= 32;
+    // The heavy pass takes items (hub, row group) instead of hubs, one per warp,
+    // and runs the general path.
+    constexpr bool heavy = PASS == 2;
+    const bool fast = MP <= 32 && K <= 32 && !heavy;
     const int CS = (K * (MP + 4) <= 32 * DS) ? MP + 4 : MP;
-    const int64_t vstep = (int64_t)gridDim.x * wpb;
-    int64_t v = a.h_lo + (int64_t)blockIdx.x * wpb + warp;
+    // t: the hub (passes 0, 1) or the item (pass 2); cof_off is read one ahead
+    const int64_t tstep = (int64_t)gridDim.x * wpb;
+    const int64_t tend = heavy ? (int64_t)*a.nitems : a.h_hi;
+    int64_t t = (heavy ? 0 : a.h_lo) + (int64_t)blockIdx.x * wpb + warp;
+    int64_t vn = 0;  // pass 2: the next item's hub
     int64_t nc0 = 0, nc1 = 0;
-    if (v < a.h_hi) {
-        nc0 = a.cof_off[v];
-        nc1 = a.cof_off[v + 1];
+    if (t < tend) {
+        if (heavy) vn = a.items[t].x;
+        nc0 = a.cof_off[heavy ? vn : t];
+        nc1 = a.cof_off[(heavy ? vn : t) + 1];
     }
-    for (; v < a.h_hi; v += vstep) {
+    for (; t < tend; t += tstep) {
+        const int64_t v = heavy ? vn : t;
         const int64_t c0 = nc0, c1 = nc1;
-        if (v + vstep < a.h_hi) {
-            nc0 = a.cof_off[v + vstep];
-            nc1 = a.cof_off[v + vstep + 1];
+        const int grp = heavy ? a.items[t].y : 0;
+        if (t + tstep < tend) {
+            if (heavy) vn = a.items[t + tstep].x;
+            nc0 = a.cof_off[heavy ? vn : t + tstep];
+            nc1 = a.cof_off[(heavy ? vn : t + tstep) + 1];
         }
-        if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
-        if (!in_phase(a.iv, a.phase, a.split_den, n, v)) continue;
+        if (!heavy) {
+            if (!a.iv.live(v)) continue;  // hub of a stopped instance (batched form)
+            if (!in_phase(a.iv, a.phase, a.split_den, n, v)) continue;
+        }
         const int64_t nrows = (int64_t)K + (c1 - c0);
+        if (PASS == 1 && nrows > kHeavyRows) continue;  // the heavy pass takes it
+        // the rows [r_lo, r_hi) this warp takes: all of the hub's, or one item's group
+        const int64_t r_lo = heavy ? (int64_t)grp * kItemRows : 0;
+        const int64_t r_hi = heavy ? min(nrows, r_lo + kItemRows) : nrows;
         // INC: no arc of the hub is new, so every pair of its tile was met through
         // arcs of G_{r-2}, in the previous round's pool, and none can change G_r
         // (the fast path reads the first 32 flags with the ids)
+        // (an item of the heavy pass: its rows and the columns, the hub's first K rows)
         if (INC && !fast) {
             bool any = false;
-            for (int64_t r = lane; r < nrows; r += 32) any |= row_new(a, v, K, c0, r) != 0;
+            for (int64_t r = lane; r < K; r += 32) any |= row_new(a, v, K, c0, r) != 0;
+            for (int64_t r = max(r_lo, (int64_t)K) + lane; r < r_hi; r += 32) any |= row_new(a, v, K, c0, r) != 0;
             if (!__any_sync(0xffffffffu, any)) continue;
         }
         // the hub's own log row: column v of the co-friend pairs, row slot 32
@@ -280,8 +324,8 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
             }
         }
 
-        for (int64_t base = 0; base < nrows; base += 32) {
-            const int nr = (int)min((int64_t)32, nrows - base);
+        for (int64_t base = r_lo; base < r_hi; base += 32) {
+            const int nr = (int)min((int64_t)32, r_hi - base);
             // stage: lane t <-> row t of the chunk
             const int64_t r = base + lane;
             int rid = -1;
@@ -294,7 +338,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                 ph = ph0;
                 roff = roff0;
             } else {
-                if (r < nrows) {
+                if (r < r_hi) {  // rows past r_hi belong to the next item
                     rid = (r < K) ? a.idx[v * K + r] : a.cof[c0 + (r - K)];
                     if (INC) rnew = row_new(a, v, K, c0, r);
                     if (!valid_id(rid, n)) {
@@ -665,15 +709,38 @@ static cudaError_t run_join(knnd_handle *h, const JoinArgs &a)
         const int threads = 128;
         const size_t smem = (size_t)S::warp_bytes(h->K) * (threads / 32);
         const bool col = has_col_offset(a.cmp);
-        auto kern = col ? (a.flag ? join_mixed_kernel<MP, true, true> : join_mixed_kernel<MP, false, true>)
-                        : (a.flag ? join_mixed_kernel<MP, true, false> : join_mixed_kernel<MP, false, false>);
+        // the heavy pass runs for the inner product, whose graphs are hub-heavy (the
+        // points of largest norm become nearly everyone's friend); the divergences'
+        // and the distance's in-degrees stay near K, where it would add two launches
+        // per join for nothing.  Incremental proposals keep one pass.
+        const bool split_heavy = !a.flag && a.cmp == KNND_CMP_INNER;
+        auto kern = split_heavy ? join_mixed_kernel<MP, false, false, 1>
+                    : col ? (a.flag ? join_mixed_kernel<MP, true, true, 0> : join_mixed_kernel<MP, false, true, 0>)
+                          : (a.flag ? join_mixed_kernel<MP, true, false, 0> : join_mixed_kernel<MP, false, false, 0>);
+        auto hkern = join_mixed_kernel<MP, false, false, 2>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(hkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (per_sm < 1) per_sm = 1;
         const int64_t need = (a.h_hi - a.h_lo + threads / 32 - 1) / (threads / 32);
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)h->num_sms * per_sm));
-        kern<<<(unsigned)grid, threads, smem, h->stream>>>(a);
+        const int64_t full = (int64_t)h->num_sms * per_sm;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, full));
+        JoinArgs m = a;
+        m.items = split_heavy ? h->heavy_items : nullptr;
+        m.nitems = h->heavy_nitems;
+        m.heavy_pass = 0;
+        if (m.items) {  // the heavy hubs' items, then the main pass, then the items
+            cudaMemsetAsync(h->heavy_nitems, 0, sizeof(int32_t), h->stream);
+            const int64_t hub_blocks = (a.h_hi - a.h_lo + 255) / 256;
+            heavy_items_kernel<<<(unsigned)std::max<int64_t>(1, hub_blocks), 256, 0, h->stream>>>(m, h->heavy_items,
+                                                                                             h->heavy_nitems);
+        }
+        kern<<<(unsigned)grid, threads, smem, h->stream>>>(m);
+        if (m.items) {
+            m.heavy_pass = 1;
+            hkern<<<(unsigned)full, threads, smem, h->stream>>>(m);
+        }
     }
     return cudaGetLastError();
 }
@@ -695,6 +762,9 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_
     a.h_hi = h_hi;
     a.phase = phase;
     a.split_den = split_den;
+    a.items = nullptr;
+    a.nitems = nullptr;
+    a.heavy_pass = 0;
     a.K = h->K;
     a.idx = idx;
     a.cof_off = h->cof_off;

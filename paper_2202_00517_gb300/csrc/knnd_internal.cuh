@@ -197,6 +197,10 @@ struct knnd_handle {
     // reverse CSR
     int32_t *deg;     // n: in-degree
     int32_t *slot;    // n*K: each arc's position in its co-friend list
+    // the mixed join's heavy hubs: items (hub, row group) and their count;
+    // capacity nK/64 + 16 >= 2nK/256 + 2nK/1025 (rows over all hubs: 2nK)
+    int2 *heavy_items;
+    int32_t *heavy_nitems;
     int64_t *cof_off; // n+1
     int32_t *cof;     // n*K
     // incremental proposals (params.incremental): the new-flag of the arc x -> v
