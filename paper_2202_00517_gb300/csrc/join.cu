@@ -9,11 +9,14 @@
 // column v for the rows of F(v).  The tile is a small dense contraction of the
 // rows' coordinates with the columns' log table: key(x, y) = negH(x) - <x, L(y)>.
 //
-// One warp per hub.  Lane j holds column j's log row in registers; the rows
-// are staged 32 at a time in shared memory and broadcast.  A pair that can
-// still beat row x's current K-th entry is appended to x's bucket (capacity
-// K*K + (K+1)*indeg(x), so it cannot overflow): one atomicAdd per (hub, row)
-// reserves the row's slots, then the surviving lanes write consecutively.
+// One warp per hub (for the inner product, hubs with very many rows go to a
+// second pass that splits their rows over several warps).  Columns' log rows
+// sit in registers (FP64 form: lane j holds column j; mixed form: a lane holds
+// a column pair of one row group); the rows are staged 32 at a time in shared
+// memory.  A pair that can still beat row x's current K-th entry is appended to
+// x's bucket (capacity K*K + (K+1)*indeg(x), so it cannot overflow): one
+// atomicAdd per (hub, row) reserves the row's slots, then the warp writes the
+// survivors consecutively.
 //
 // FP64 form: key in FP64, exact filter (key, y) < (tau_x, idxK_x); the entry
 // stores the key (bkey) and its FP32 round-up.
