@@ -350,7 +350,7 @@ def gpu_single(args, name, rank, world, local, barrier):
         "join_survivors_per_build": info["join_survivors"],
         "phase_ms_per_build": {p: st["phase_ms"][p] / steps for p in st["phase_ms"]},
         "phase_share": {p: st["phase_ms"][p] / total_ph for p in st["phase_ms"]},
-        "roofline": {"kernel": f"join_mixed_kernel<{MP}, 0, 0>" if args.form == "mixed" else f"join_tc_kernel<{MP}>",
+        "roofline": {"kernel": f"join_mixed_kernel<{MP}, 0, 0, 0>" if args.form == "mixed" else f"join_tc_kernel<{MP}>",
                      "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
