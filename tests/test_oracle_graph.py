@@ -186,6 +186,28 @@ def _cayley(n, A):
     return ((np.arange(n)[:, None] + A[None, :]) % n).astype(np.int32)
 
 
+def test_ties_ordered_by_index():
+    # Exact copies of a point key to exactly 0 against it (the same chain on the
+    # same numbers), so equal keys meet; the order is (key, index) ascending.
+    n, K = 300, 8
+    p = dirichlet_points(n, 6, 8, np.float64)
+    dups = [17, 45, 101, 150, 299]
+    p[dups] = p[3]
+    bi, bk = oracle.bruteforce(p, K, [3])
+    assert list(bi[0, :5]) == dups and np.all(bk[0, :5] == 0.0)
+    assert np.all(bk[0, 5:] > 0.0)
+    # a copy sees the original and the other copies, lowest index first
+    bi, bk = oracle.bruteforce(p, K, [150])
+    assert list(bi[0, :5]) == [3, 17, 45, 101, 299] and np.all(bk[0, :5] == 0.0)
+    # a round on many copies meets ties and still orders them by index
+    q = dirichlet_points(n, 6, 9, np.float64)
+    q[1::3] = q[0::3][: len(q[1::3])]
+    g0, _ = oracle.init_graph(q, K, 9)
+    idx, key, _, _, _ = oracle.round_(q, g0)
+    _check_rows(idx, key, n, K)
+    assert np.any(np.diff(key, axis=1) == 0)
+
+
 def test_fcc_complete_graph_always_hits():
     K = 6
     idx = np.array([[y for y in range(K + 1) if y != x] for x in range(K + 1)], dtype=np.int32)
@@ -223,6 +245,23 @@ def test_fcc_random_graph_rate():
     h = oracle.fcc(idx, 0, 0, S)
     rate = 2 * K / (n - 1)
     assert abs(h - S * rate) < 5 * np.sqrt(S * rate)
+
+
+def test_fcc_rounds_draw_fresh_samples():
+    # The clustering rate is estimated afresh in every round (Sec. 3.3): on one
+    # fixed graph with exact hit rate 2/3 (generators {1, 2, 4}), the counts of
+    # forty rounds scatter like independent binomial draws, not like one draw
+    # repeated.
+    n, S, R = 997, 2000, 40
+    idx = _cayley(n, [1, 2, 4])
+    h = np.array([oracle.fcc(idx, 6, r, S) for r in range(R)], dtype=np.float64)
+    p = 2 / 3
+    assert abs(h.mean() - S * p) < 5 * np.sqrt(S * p * (1 - p) / R)
+    ratio = h.var(ddof=1) / (S * p * (1 - p))
+    lo, hi = stats.chi2.ppf([1e-6, 1 - 1e-6], R - 1) / (R - 1)
+    assert lo < ratio < hi
+    # the seed enters every sample as well
+    assert [oracle.fcc(idx, 7, r, S) for r in range(4)] != list(h[:4].astype(int))
 
 
 # ---------------------------------------------------------------- diameter

@@ -94,3 +94,15 @@ def test_delta_proportion_stop_truncates_the_build():
     assert np.array_equal(d["idx"], cut["idx"]) and np.array_equal(d["key"], cut["key"])
     # delta = 0 is off
     assert oracle.build(p, K, seed, S=2000, stop_on_zero=False, stop_delta=0.0)["rounds"] == full["rounds"]
+
+
+def test_stop_when_hits_tie():
+    # Sec. 3.3: the build ends after the first round whose clustering hits do not
+    # rise; equal counts do not rise.  With n = K + 1 the initial graph is already
+    # complete, every sample hits before and after round 1 (S = S), so the build
+    # stops after round 1 even with the zero-update stop switched off.
+    n, K, S = 9, 8, 500
+    p = dirichlet_points(n, 4, 12, np.float64)
+    res = oracle.build(p, K, 12, S=S, max_rounds=6, stop_on_zero=False)
+    assert list(res["hits"]) == [S, S]
+    assert res["rounds"] == 1 and list(res["updates"]) == [0]

@@ -81,3 +81,14 @@ def test_bounded_rejection_heavy_range():
     assert abs(d.mean() / N - 0.5) < 0.01
     counts = np.bincount((d // (N / 16)).astype(np.int64), minlength=16)
     assert stats.chisquare(counts).pvalue > 1e-4
+
+
+def test_bounded_unbiased_where_truncation_is_worst():
+    # N = ceil(2^33 / 3): 2^32 / N = 1.5, so the multiply-shift map without its
+    # rejection step gives every even value two words and every odd value one
+    # (two thirds of the draws even).  With rejection every value has the same
+    # number of accepted words: half even, within sampling error.
+    N = 0xAAAAAAAB
+    d = oracle.bounded_draws(5, 0, 0, 0, N, 40_000).astype(np.int64)
+    assert d.max() < N
+    assert abs(np.mean(d % 2 == 0) - 0.5) < 0.015
