@@ -52,6 +52,7 @@ WORKLOADS = {
 }
 N, M, K, SEED, WORKLOAD = WORKLOADS["n1e6_d20_K20"]
 REF_ROWS = 100_000  # rows of round 1 the oracle computes per reference step
+UNIQUE_ROWS = 10_000  # rows of round 1 whose distinct pairs the CPU leg counts
 
 
 def evals_of(n, k, rounds):
@@ -147,6 +148,35 @@ def cpu_reference_step(pts64, g0i):
     _, _, _, _, props = oracle.round_(pts64, g0i, 0, REF_ROWS)
     dt = time.perf_counter() - t0
     return props, dt
+
+
+def cpu_pair_counts(g0i, rows=UNIQUE_ROWS):
+    """Pairs of round 1 for rows [0, rows), from the oracle's initial graph g0i: the
+    multiset the metric counts (K^2 + (K+1)*indeg(x) per row) and the distinct
+    pairs among them (the size of each row's candidate pool)."""
+    import oracle
+    n, K = g0i.shape
+    deg = oracle.indegree(g0i)[:rows].astype(np.int64)
+    multiset = int((K * K + (K + 1) * deg).sum())
+    unique = int(sum(len(p) for p in oracle.pools(g0i, 0, rows)))
+    return {"rows": rows, "multiset": multiset, "unique": unique, "unique_fraction": unique / multiset}
+
+
+def cpu_pair_trend(m, K, seed, n=10_000):
+    """Fraction of distinct pairs in each round's multiset over a whole oracle
+    build of a small instance of the same shape (n points, m coordinates, K):
+    round 1 starts from a random graph whose friend lists barely overlap; as the
+    graph clusters, friends of friends repeat."""
+    import oracle
+    p = dirichlet_points(n, m, seed, np.float64)
+    rounds = oracle.build(p, K, seed, S=10000)["rounds"]
+    g, _ = oracle.init_graph(p, K, seed)
+    frac = []
+    for _ in range(rounds):
+        multiset = int((K * K + (K + 1) * oracle.indegree(g)).sum())
+        frac.append(round(sum(len(q) for q in oracle.pools(g)) / multiset, 4))
+        g = oracle.round_(p, g)[0]
+    return {"n": n, "m": m, "K": K, "rounds": rounds, "unique_fraction": frac}
 
 
 def run_reference(args, rank, world):
@@ -412,7 +442,9 @@ def gpu_single(args, name, rank, world, local, barrier):
         line["cpu_baseline"] = {
             "value": e / s, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": (f"oracle round 1 for rows [0, {REF_ROWS}) of the n=1e6 workload from its own initial "
-                       f"graph ({e} evaluations in {s:.2f} s, setup over all n included)")}
+                       f"graph ({e} evaluations in {s:.2f} s, setup over all n included)"),
+            "pairs_round1": cpu_pair_counts(g0i),
+            "pairs_by_round_small": cpu_pair_trend(M, K, SEED)}
     return line
 
 

@@ -1,0 +1,47 @@
+"""Host-side figures of the benchmark's CPU leg: the pair counts reported beside
+the KL-evaluation metric.  The multiset is what a round scores (K^2 + (K+1)*indeg(x)
+proposals per row, the per-point K + 2K^2 of the footnote in Sec. 4.4 on average);
+the distinct pairs are the candidate pools of Sec. 3.1, enumerated here with
+Python sets."""
+import numpy as np
+
+import bench
+import oracle
+from paper_2202_00517_gb300.datagen import dirichlet_points
+
+
+def _pool_sets(idx, rows):
+    n, K = idx.shape
+    co = [[] for _ in range(n)]
+    for x in range(n):
+        for v in idx[x]:
+            co[v].append(x)
+    out = []
+    for x in range(rows):
+        s = set(idx[x]) | set(co[x])
+        for v in idx[x]:
+            s |= set(idx[v])
+        for w in co[x]:
+            s |= set(idx[w])
+        s.discard(x)
+        out.append(s)
+    return out
+
+
+def test_pair_counts_match_enumeration():
+    n, m, K, seed, rows = 3000, 6, 10, 4, 500
+    p = dirichlet_points(n, m, seed, np.float64)
+    g, _ = oracle.init_graph(p, K, seed)
+    c = bench.cpu_pair_counts(g, rows)
+    _, _, _, _, props = oracle.round_(p, g, 0, rows)
+    assert c["multiset"] == props
+    assert c["unique"] == sum(len(s) for s in _pool_sets(g, rows))
+    assert 0 < c["unique_fraction"] <= 1
+
+
+def test_pair_trend_falls_as_the_graph_clusters():
+    t = bench.cpu_pair_trend(6, 10, 4, n=3000)
+    f = t["unique_fraction"]
+    assert len(f) == t["rounds"] >= 2
+    assert all(0 < x <= 1 for x in f)
+    assert f[-1] < f[0]
