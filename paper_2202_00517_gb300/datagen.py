@@ -80,6 +80,16 @@ def dirichlet_points(n: int, m: int, seed: int, dtype=np.float32, chunk: int = 1
     return out
 
 
+def skewed_points(n: int, m: int, seed: int, power: float, dtype=np.float32) -> np.ndarray:
+    """Points near the faces of the simplex: the Dirichlet(1) points of
+    `dirichlet_points`, each coordinate raised to `power` in float64 and the row
+    renormalised to sum 1, then stored in the requested dtype.  For power > 1 a
+    few coordinates carry most of each row's mass and the rest spread over many
+    orders of magnitude (down to about 1e-40 at power 8 and m = 11)."""
+    x = dirichlet_points(n, m, seed, np.float64) ** power
+    return (x / x.sum(axis=1, keepdims=True)).astype(dtype)
+
+
 def instance_mix(count: int, seed: int):
     """Shapes of a batch of independent instances: n log-uniform in [200, 50000],
     m in {6, 11, 21}, K in {8, 16, 32}, each uniform, drawn from the Philox stream

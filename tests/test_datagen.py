@@ -4,7 +4,7 @@ marginal is Beta(1, m-1), with CDF 1 - (1 - t)^(m-1))."""
 import numpy as np
 from scipy import stats
 
-from paper_2202_00517_gb300.datagen import dirichlet_points, instance_mix
+from paper_2202_00517_gb300.datagen import dirichlet_points, instance_mix, skewed_points
 
 
 def test_points_on_simplex_and_reproducible():
@@ -43,3 +43,13 @@ def test_threads_and_chunks_do_not_change_values():
     a = dirichlet_points(3000, 7, 9, np.float32)
     b = dirichlet_points(3000, 7, 9, np.float32, chunk=256, threads=4)
     assert np.array_equal(a, b)
+
+
+def test_skewed_points():
+    p = skewed_points(500, 11, 3, 16, np.float64)
+    assert p.shape == (500, 11) and np.all(p > 0)
+    assert np.allclose(p.sum(1), 1.0, rtol=0, atol=1e-15)
+    # most of each row's mass on few coordinates, the rest over many decades
+    assert np.median(p.max(1)) > 0.5 and p.min() < 1e-40
+    q = dirichlet_points(500, 11, 3, np.float64) ** 16
+    assert np.array_equal(p, q / q.sum(1, keepdims=True))

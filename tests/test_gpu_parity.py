@@ -10,13 +10,14 @@
   graph is not proposed again) give the same graph as proposing every pair;
   lockstep rounds run both ways against the oracle's full pool;
 * shapes spanning several warps/tiles with ragged tails, K from 2 to 64, m from
-  1 (every key ties) to 128, n = K+1, duplicated points (exact ties).
+  1 (every key ties) to 128, n = K+1, duplicated points (exact ties), points near
+  the simplex's faces (coordinates that underflow in the FP32 filter).
 """
 import numpy as np
 import pytest
 
 import oracle
-from paper_2202_00517_gb300.datagen import dirichlet_points
+from paper_2202_00517_gb300.datagen import dirichlet_points, skewed_points
 from parity_util import check_invariants, compare_graphs
 
 torch = pytest.importorskip("torch")
@@ -120,6 +121,32 @@ def test_shapes_lockstep(knnd, n, m, K, seed, dtype, prec):
     pts = dirichlet_points(n, m, seed, np.float32 if dtype == "f32" else np.float64)
     ties = _lockstep(knnd, pts, K, seed, prec, rounds=3, dtype=dtype, S=500)
     assert ties <= max(2, n // 500)
+
+
+@pytest.mark.parametrize("dtype,power", [("f64", 16), ("f32", 4)])
+@pytest.mark.parametrize("prec", PRECS)
+def test_skewed_points_lockstep(knnd, prec, dtype, power):
+    # Points near the faces of the simplex.  In FP64 (power 16) coordinates go down
+    # to about 1e-73: the filter's FP32 copy turns some into subnormals and some
+    # into 0, and |log y| reaches about 170, so the FP32 bound is wide and most
+    # pairs reach the FP64 re-score.  The graphs must still be the oracle's, with
+    # no audited bound violation, and every form must equal the FP64 form.
+    n, m, K, seed = 1500, 11, 16, 31
+    pts = skewed_points(n, m, seed, power, np.float64 if dtype == "f64" else np.float32)
+    assert np.all(pts > 0)
+    if dtype == "f64":
+        assert np.any(pts.astype(np.float32) == 0)  # the case this test is for
+    ties = _lockstep(knnd, pts, K, seed, prec, rounds=3, dtype=dtype, S=500)
+    assert ties <= max(2, n // 500)
+    p = _dev(pts)
+    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, debug=True)
+    out = h.build(p, seed)
+    h.close()
+    assert out["bound_violations"] == 0
+    ref = knnd.Handle(n, m, K, dtype=dtype, precision="fp64")
+    r = ref.build(p, seed)
+    ref.close()
+    assert torch.equal(out["idx"], r["idx"]) and torch.equal(out["key"], r["key"])
 
 
 @pytest.mark.parametrize("prec", PRECS)
