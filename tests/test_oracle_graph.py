@@ -264,6 +264,22 @@ def test_fcc_rounds_draw_fresh_samples():
     assert [oracle.fcc(idx, 7, r, S) for r in range(4)] != list(h[:4].astype(int))
 
 
+def test_fcc_draws_x_over_all_points():
+    # Sec. 3.3 samples x uniformly from all n points.  Points 0..499 sit in cliques
+    # of five (any two friends are friends: always a hit); points 500..999 form a
+    # ring with odd offsets {1, 3, 5, 7} (two friends differ by an even step, never
+    # a friend: never a hit).  The hit rate is exactly 1/2.
+    n, K, S = 1000, 4, 20000
+    idx = np.zeros((n, K), dtype=np.int32)
+    for x in range(500):
+        b = x - x % 5
+        idx[x] = [y for y in range(b, b + 5) if y != x]
+    for x in range(500, 1000):
+        idx[x] = [500 + (x - 500 + a) % 500 for a in (1, 3, 5, 7)]
+    h = oracle.fcc(idx, 5, 1, S)
+    assert abs(h - S / 2) < 5 * np.sqrt(S / 4)
+
+
 # ---------------------------------------------------------------- diameter
 @pytest.mark.parametrize("n,K,seed", [(200, 3, 1), (500, 4, 2), (1200, 3, 3)])
 def test_diameter_matches_networkx(n, K, seed):
@@ -283,3 +299,33 @@ def test_diameter_path_graph():
     n = 101
     idx = ((np.arange(n) + 1) % n).astype(np.int32)[:, None]
     assert oracle.diameter_exact(idx) == n // 2
+
+
+def test_diameter_disconnected_graph():
+    # two disjoint 3-out rings: no path between them, so no finite diameter
+    n, K = 400, 3
+    idx = np.zeros((n, K), dtype=np.int32)
+    for x in range(n):
+        b = 0 if x < 200 else 200
+        idx[x] = [b + (x - b + a) % 200 for a in (1, 2, 3)]
+    assert oracle.diameter_exact(idx) == -1
+    assert oracle.diameter_bounds(idx, 4, 1) == (-1, -1)
+    # joined by one arc the graph is connected again
+    idx[0, 0] = 200
+    assert oracle.diameter_exact(idx) > 0
+
+
+def test_diameter_bounds_use_every_sweep():
+    # Every double sweep raises the lower bound to the largest eccentricity seen:
+    # on sparse random graphs one sweep finds the exact diameter less than half
+    # the time, twenty sweeps nearly always; every bracket holds.
+    hits = 0
+    for seed in range(40):
+        p = dirichlet_points(300, 3, seed, np.float64)
+        g, _ = oracle.init_graph(p, 2, seed)
+        ex = oracle.diameter_exact(g)
+        lo1, hi1 = oracle.diameter_bounds(g, 1, seed)
+        lo, hi = oracle.diameter_bounds(g, 20, seed)
+        assert lo1 <= lo <= ex <= hi <= hi1
+        hits += lo == ex
+    assert hits >= 32

@@ -10,6 +10,9 @@ Each case plants one plausible mistake in a copy of the oracle's C source:
 - a changed clustering sample or stop rule (Sec. 3.3, Table 1);
 - a wrong brute-force K-NN (Sec. 2.3) or diameter (Sec. 4.3).
 
+Mistakes that make the oracle loop forever or crash are left out: they cannot pass
+the pins, but they would only slow this check down.
+
 The copy is compiled in a scratch folder, and the oracle pin files run against it in
 a child process.  Every mutant must make them fail, and the unchanged copy must pass.
 The mistakes are planted on the CPU, in the copy only.
@@ -70,6 +73,26 @@ MUTANTS = [
     ("diameter_upper_bound", "if (best_hi < 0 || 2 * e < best_hi) best_hi = 2 * e;",
      "if (best_hi < 0 || e < best_hi) best_hi = e;"),
     ("bfs_ecc_off_by_one", "dist[w] = dist[v] + 1;", "dist[w] = dist[v] + (dist[v] > 0 ? 1 : 2);"),
+    ("init_keys_swapped", "c[cnt].key = orc_key_from_tables(pts, L, negH, m, x, y);",
+     "c[cnt].key = orc_key_from_tables(pts, L, negH, m, y, x);"),
+    ("seed_words_swapped", "s->key[0] = (uint32_t)(seed & 0xffffffffu);\n    s->key[1] = (uint32_t)(seed >> 32);",
+     "s->key[1] = (uint32_t)(seed & 0xffffffffu);\n    s->key[0] = (uint32_t)(seed >> 32);"),
+    ("stream_block_not_advanced", "        s->block += 1;\n", "        s->block += 0;\n"),
+    ("delta_rule_inclusive", "if (stop_delta > 0.0 && (double)updates[r - 1] < stop_delta",
+     "if (stop_delta > 0.0 && (double)updates[r - 1] <= stop_delta"),
+    ("stop_on_zero_ignored", "if (stop_on_zero && updates[r - 1] == 0) break;",
+     "if (0 && stop_on_zero && updates[r - 1] == 0) break;"),
+    ("hits0_round_one", "hits[0] = orc_fcc(idx, n, K, seed, 0, S);", "hits[0] = orc_fcc(idx, n, K, seed, 1, S);"),
+    ("sqe_col_norm_dropped", "return (off[x] - 2.0 * dot) + off[y];", "return (off[x] - 2.0 * dot) + 0.0 * off[y];"),
+    ("sqe_row_norm_dropped", "return (off[x] - 2.0 * dot) + off[y];", "return (0.0 - 2.0 * dot) + off[y];"),
+    ("inner_offset_one", "            off[y] = 0.0;", "            off[y] = 1.0;"),
+    ("fcc_i_range_short", "int i = (int)orc_bounded(&st, (uint32_t)K);", "int i = (int)orc_bounded(&st, (uint32_t)(K - 1));"),
+    ("fcc_x_range_short", "int64_t x = orc_bounded(&st, (uint32_t)n);", "int64_t x = orc_bounded(&st, (uint32_t)(n / 2));"),
+    ("bruteforce_partial_sort",
+     "qsort(c, (size_t)len, sizeof(orc_cand), orc_cand_cmp);\n            for (int t = 0; t < K; ++t) {\n                idx[q * K + t]",
+     "qsort(c, (size_t)(len / 2), sizeof(orc_cand), orc_cand_cmp);\n            for (int t = 0; t < K; ++t) {\n                idx[q * K + t]"),
+    ("bfs_disconnected_ignored", "return tail == n ? ecc : -1;", "return ecc;"),
+    ("diameter_lower_from_first_sweep_only", "if (e > best_lo) best_lo = e;", "if (t == 0 && e > best_lo) best_lo = e;"),
 ]
 
 

@@ -106,3 +106,47 @@ def test_stop_when_hits_tie():
     res = oracle.build(p, K, 12, S=S, max_rounds=6, stop_on_zero=False)
     assert list(res["hits"]) == [S, S]
     assert res["rounds"] == 1 and list(res["updates"]) == [0]
+
+
+def test_delta_rule_is_strict():
+    # Dong et al.'s rule stops after a round with FEWER than delta*n*K updates.  With
+    # n*K a power of two, delta*n*K equals a round's update count exactly, and that
+    # round does not stop the build: the first round strictly below it does.
+    n, m, K, seed = 2048, 6, 8, 3
+    p = dirichlet_points(n, m, seed, np.float64)
+    upd = list(oracle.build(p, K, seed, S=2000, stop_on_zero=False)["updates"])
+    u = upd[1]
+    below = next(r for r in range(2, len(upd)) if upd[r] < u)
+    d = oracle.build(p, K, seed, S=2000, stop_on_zero=False, stop_delta=u / (n * K))
+    assert u / (n * K) * (n * K) == u
+    assert d["rounds"] == below + 1
+
+
+def test_zero_update_stop():
+    # With the zero-update stop on, the build ends at the first round that changes
+    # nothing, even while the clustering hits still rise (seed 25 of this shape:
+    # round 4 makes no update and its hits rise from 124 to 140).
+    n, m, K, seed = 80, 3, 5, 25
+    p = dirichlet_points(n, m, seed, np.float64)
+    free = oracle.build(p, K, seed, S=200, stop_on_zero=False, max_rounds=12)
+    u, h = list(free["updates"]), list(free["hits"])
+    r0 = u.index(0) + 1
+    assert h[r0] > h[r0 - 1] and free["rounds"] > r0
+    z = oracle.build(p, K, seed, S=200, stop_on_zero=True, max_rounds=12)
+    assert z["rounds"] == r0 and list(z["updates"]) == u[:r0]
+
+
+@pytest.mark.parametrize("seed", [7, 8, 9])
+def test_build_is_its_steps(seed):
+    # Sec. 3: a build is the initial graph, then synchronous rounds, with the
+    # clustering sample of round r (round 0: the initial graph) after each.
+    n, m, K, S = 600, 5, 8, 2000
+    p = dirichlet_points(n, m, seed, np.float64)
+    b = oracle.build(p, K, seed, S=S)
+    g, _ = oracle.init_graph(p, K, seed)
+    assert b["hits"][0] == oracle.fcc(g, seed, 0, S)
+    for r in range(1, b["rounds"] + 1):
+        g, key, _, upd, _ = oracle.round_(p, g)
+        assert b["updates"][r - 1] == upd
+        assert b["hits"][r] == oracle.fcc(g, seed, r, S)
+    assert np.array_equal(b["idx"], g) and np.array_equal(b["key"], key)
