@@ -45,3 +45,33 @@ def test_pair_trend_falls_as_the_graph_clusters():
     assert len(f) == t["rounds"] >= 2
     assert all(0 < x <= 1 for x in f)
     assert f[-1] < f[0]
+
+
+def test_traffic_read_only_for_the_profiled_source(tmp_path, monkeypatch):
+    # The roofline's DRAM traffic comes from a committed ncu summary, and only while
+    # the join source it was taken on is the current one (its sha256 recorded there).
+    import hashlib
+    src = tmp_path / "paper_2202_00517_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (src / "join.cu").write_text("// join v1\n")
+    sha = hashlib.sha256(b"// join v1\n").hexdigest()
+    (tmp_path / "profiles" / "join_mixed_w.md").write_text(
+        f"join.cu sha256: {sha}\n\ndram bytes per full-size launch: 9.5e+09\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.join_traffic_per_launch("w") == 9.5e9
+    assert bench.join_traffic_per_launch("other") is None
+    (src / "join.cu").write_text("// join v2\n")
+    assert bench.join_traffic_per_launch("w") is None
+
+
+def test_committed_profile_matches_the_join_source():
+    # the benchmark workload's summary parses; its traffic is the join's, a few GB
+    t = bench.join_traffic_per_launch("n1e6_d20_K20")
+    assert t is None or 1e9 < t < 1e11
+
+
+def test_evaluation_count():
+    # n K initial keys plus n (K + 2 K^2) proposals per round (Sec. 4.4 footnote)
+    assert bench.evals_of(10, 2, 0) == 20
+    assert bench.evals_of(10, 2, 3) == 20 + 3 * 10 * (2 + 8)
