@@ -34,6 +34,12 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _require(ok: bool, msg: str):
+    """Argument checks that hold under python -O too (unlike assert)."""
+    if not ok:
+        raise ValueError(msg)
+
+
 def _info_dict(info: _lib.knnd_build_info) -> dict:
     r = info.rounds
     return {"rounds": r, "stop_reason": info.stop_reason,
@@ -79,8 +85,11 @@ class Handle:
         check(self._lib.knnd_set_stream(self._h, _stream_ptr(stream)), "knnd_set_stream")
 
     def _check_points(self, points):
-        assert points.is_cuda and points.dtype == self.torch_dtype and points.dim() == 2
-        assert points.shape[0] == self.n and points.shape[1] >= self.m and points.stride(1) == 1
+        _require(points.is_cuda, "points must be a CUDA tensor")
+        _require(points.dtype == self.torch_dtype, f"points must be {self.torch_dtype}")
+        _require(points.dim() == 2 and points.shape[0] == self.n and points.shape[1] >= self.m,
+                 f"points must be ({self.n}, >= {self.m})")
+        _require(points.stride(1) == 1, "each point's coordinates must be contiguous")
         return points.stride(0)
 
     def new_graph(self, device=None):
@@ -127,7 +136,11 @@ class Handle:
 
     def build_host(self, points_host, seed: int, idx_host=None, key_host=None) -> dict:
         """Build from host memory (pinned for full bandwidth); returns host idx/key."""
-        assert not points_host.is_cuda and points_host.dtype == self.torch_dtype
+        _require(not points_host.is_cuda, "points_host must be a host tensor")
+        _require(points_host.dtype == self.torch_dtype, f"points_host must be {self.torch_dtype}")
+        _require(points_host.dim() == 2 and points_host.shape[0] == self.n and points_host.shape[1] >= self.m,
+                 f"points_host must be ({self.n}, >= {self.m})")
+        _require(points_host.stride(1) == 1, "each point's coordinates must be contiguous")
         ld = points_host.stride(0)
         if idx_host is None:
             idx_host = torch.empty((self.n, self.K), dtype=torch.int32, pin_memory=True)
@@ -175,12 +188,17 @@ def build_batched(points_list, Ks, seeds, precision: str = "mixed", fcc_samples:
     """
     lib = _lib.load()
     count = len(points_list)
+    _require(count > 0, "need at least one instance")
+    _require(len(Ks) == count and len(seeds) == count, "one K and one seed per instance")
+    _require(outputs is None or len(outputs) == count, "one (idx, key) pair per instance")
     dt = points_list[0].dtype
     dtype = _DTYPE[dt]
     arr = (_lib.knnd_instance * count)()
     outs = []
     for i, (p, K, sd) in enumerate(zip(points_list, Ks, seeds)):
-        assert p.is_cuda and p.dtype == dt and p.dim() == 2 and p.stride(1) == 1
+        _require(p.is_cuda and p.dim() == 2 and p.stride(1) == 1,
+                 f"instance {i}: points must be a 2-D CUDA tensor with contiguous rows")
+        _require(p.dtype == dt, f"instance {i}: every instance must have the dtype of the first")
         n, m = p.shape
         if outputs is not None:
             idx, key = outputs[i]

@@ -103,3 +103,28 @@ def test_product_path_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_binding_argument_checks(lib):
+    # the Python binding rejects bad tensors itself (ValueError, also under
+    # python -O) before the library or a device is reached
+    import torch
+
+    from paper_2202_00517_gb300 import api
+    p = torch.rand(50, 4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        api.build_batched([], [], [])
+    with pytest.raises(ValueError):
+        api.build_batched([p, p], [5], [1, 2])      # one K for two instances
+    with pytest.raises(ValueError):
+        api.build_batched([p], [5], [1])            # host tensor
+    h = api.Handle.__new__(api.Handle)              # no device: checks only
+    h.n, h.m, h.K, h.torch_dtype = 50, 4, 5, torch.float64
+    with pytest.raises(ValueError):
+        h._check_points(p)                          # host tensor
+    with pytest.raises(ValueError):
+        h.build_host(p.t().contiguous().t(), 1)     # coordinates not contiguous
+    with pytest.raises(ValueError):
+        h.build_host(p[:40], 1)                     # wrong n
+    with pytest.raises(ValueError):
+        h.build_host(p.float(), 1)                  # wrong dtype
