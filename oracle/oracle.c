@@ -249,8 +249,8 @@ static int orc_int_cmp(const void *a, const void *b)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Initial graph (Sec. 3.2; Sec. 4.2): each x selects K distinct elements of */
-/* S \ {x} uniformly at random; the friend list is then ordered by x's       */
+/* Initial graph (Sec. 3.2; Sec. 4.2): x draws K distinct friends from the   */
+/* other n - 1 points, each equally likely, and orders them by its           */
 /* comparator.  Draw: y' uniform in [0, n-1), y = y' + (y' >= x); a value    */
 /* already chosen is drawn again.                                            */
 /* ------------------------------------------------------------------------ */

@@ -4,8 +4,8 @@
   within 2 ceil(log_K n) rounds and the final friend clustering rate lies near the
   printed value (tolerance: the paper's own spread across n and K plus sampling
   noise of the rate, +-0.05).
-* Sec. 3.2 / Sec. 4.3: the number of rounds does not exceed twice the diameter of
-  the undirected initial graph (diameter by BFS).
+* Sec. 3.2 / Sec. 4.3: a build takes at most 2 diam(G0) rounds, where diam(G0) is
+  the diameter of the initial graph with its arcs read as undirected edges (by BFS).
 * Sec. 3.3 (iii): the clustering rate starts near zero (2K/n for a random K-out
   graph) and rises before it plateaus.
 * Sec. 4.4 item 4: recall of the true K nearest neighbours is high at 10
