@@ -16,8 +16,8 @@
  *   - one round (Sec. 3.1, Sec. 4.2): every x meets its co-friends, its
  *     friends' friends and its co-friends' friends; its new friend list is the
  *     K best of those and its old friends; all lists change together;
- *   - termination (Sec. 3.3): a sampled friend clustering rate; stop at the
- *     first round at which it does not increase.
+ *   - termination (Sec. 3.3): a sampled friend clustering rate; the build
+ *     ends with the first round whose rate is no higher than the last one's.
  *
  * Conventions shared by every call:
  *   - Points: n rows of m coordinates, row-major with a leading dimension of

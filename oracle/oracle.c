@@ -539,8 +539,8 @@ void orc_bruteforce(const double *pts, int64_t n, int m, int K, const int32_t *q
 }
 
 /* ------------------------------------------------------------------------ */
-/* Diameter of the undirected version of a K-out digraph (Sec. 3.2; Sec.     */
-/* 4.3), by breadth-first search.                                            */
+/* Diameter of a K-out digraph with its arcs read as undirected edges       */
+/* (Sec. 3.2; Sec. 4.3), by breadth-first search.                            */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int64_t *off;

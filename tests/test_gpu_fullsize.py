@@ -8,8 +8,8 @@ The oracle cannot run the whole build at this size within a test, so:
   on sampled row ranges the oracle computes one by one;
 * the free-running builds are checked by properties that hold at any size:
   row invariants, the mixed form equal to the FP64 form bit for bit, the stop
-  rule, rounds within twice the diameter of the undirected initial graph
-  (Sec. 3.2, Sec. 4.3), and recall against brute force on sampled queries.
+  rule, at most 2 diam(G0) rounds with diam(G0) taken over the initial graph's arcs
+  as undirected edges (Sec. 3.2, Sec. 4.3), and recall against brute force on sampled queries.
 """
 import numpy as np
 import pytest
@@ -77,7 +77,7 @@ def test_full_builds(data):
     assert b["stop_reason"] in (1, 2)
     if b["stop_reason"] == 1:
         assert h[r] <= h[r - 1] and all(h[t] > h[t - 1] for t in range(1, r))
-    # rounds vs twice the diameter of the undirected initial graph (lower bound of the diameter)
+    # rounds vs 2 diam(G0), arcs as undirected edges (a lower bound of the diameter suffices)
     lo, hi = oracle.diameter_bounds(g0i, sweeps=2, seed=SEED)
     assert lo > 0
     assert r <= 2 * lo, (r, lo, hi)
