@@ -434,7 +434,7 @@ def gpu_single(args, name, rank, world, local, barrier):
         line["evals_per_s_fp64"] = world * fp64["evals"] / (fp64_ms / 1e3)
         line["speedup_mixed_vs_fp64"] = line["build_s_fp64"] / line["build_s_mixed"]
         line["fp64_join_ms_per_launch"] = fp64["stats"]["phase_ms"]["join"] / max(1, fp64["stats"]["phase_count"]["join"])
-    if not args.no_cpu_baseline and name == "n1e6_d20_K20":
+    if not args.no_cpu_baseline and name == "n1e6_d20_K20" and world == 1:  # rank 0 at N = 1 only
         import oracle
         pts64 = pts_host.numpy().astype(np.float64)
         g0i, _ = oracle.init_graph(pts64, K, SEED)
