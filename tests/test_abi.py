@@ -128,3 +128,17 @@ def test_binding_argument_checks(lib):
         h.build_host(p[:40], 1)                     # wrong n
     with pytest.raises(ValueError):
         h.build_host(p.float(), 1)                  # wrong dtype
+
+
+def test_header_constants_match_the_binding():
+    # every integer #define of include/knnd.h has the same value in the binding
+    text = open(HEADER).read()
+    found = 0
+    for name, expr in re.findall(r"^#define\s+(KNND_[A-Z0-9_]+)\s+([-()0-9<\s]+?)\s*(?:/\*.*)?$", text, flags=re.M):
+        value = eval(expr, {"__builtins__": {}})  # digits, parentheses, minus and shifts only
+        if name.startswith("KNND_PHASE_"):
+            assert _lib.PHASES[value] == name[len("KNND_PHASE_"):].lower(), name
+        else:
+            assert getattr(_lib, name) == value, name
+        found += 1
+    assert found >= 35
