@@ -142,3 +142,22 @@ def test_header_constants_match_the_binding():
             assert getattr(_lib, name) == value, name
         found += 1
     assert found >= 35
+
+
+def test_header_structs_match_the_binding():
+    # field names, order and widths of every struct of include/knnd.h equal the
+    # binding's ctypes layout (a size check alone misses two swapped fields)
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    width = {"int32_t": 4, "int64_t": 8, "uint64_t": 8, "float": 4, "double": 8}
+    consts = {k: getattr(_lib, k) for k in dir(_lib) if k.startswith("KNND_")}
+    structs = re.findall(r"typedef struct\s*\{(.*?)\}\s*(knnd_\w+)\s*;", text, flags=re.S)
+    assert {s for _, s in structs} >= {"knnd_params", "knnd_build_info", "knnd_stats", "knnd_instance"}
+    for body, name in structs:
+        fields = re.findall(r"([\w\s]+?\*?)\s*\b(\w+)\s*(?:\[([^\]]+)\])?\s*;", body)
+        py = getattr(_lib, name)._fields_
+        assert [f[1] for f in fields] == [f[0] for f in py], name
+        for (ctype, fname, dim), (_, pytype) in zip(fields, py):
+            ctype = ctype.replace("const", "").strip()
+            n = eval(dim, {"__builtins__": {}}, consts) if dim else 1
+            w = 8 if ctype.endswith("*") else width[ctype]
+            assert ctypes.sizeof(pytype) == w * n, f"{name}.{fname}"
