@@ -161,3 +161,20 @@ def test_header_structs_match_the_binding():
             n = eval(dim, {"__builtins__": {}}, consts) if dim else 1
             w = 8 if ctype.endswith("*") else width[ctype]
             assert ctypes.sizeof(pytype) == w * n, f"{name}.{fname}"
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    # no silent fallback: without the built CUDA library the binding raises
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load(os.path.join(ROOT, "no_such_dir", "libknnd.so"))
+
+
+def test_binding_signatures_match_the_prototypes(lib):
+    # each function the binding types takes as many arguments as its prototype
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = dict(re.findall(r"\b(knnd_[a-z_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S))
+    for name in _lib.EXPORTS:
+        args = protos[name].strip()
+        n = 0 if args in ("", "void") else args.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, name
