@@ -247,19 +247,38 @@ knnd_status knnd_build_host(knnd_handle *h, const void *points_host, int64_t ld,
  * that forbids allocation after start-up, a plug-in whose host requires all
  * allocations to go through the host's allocator -- and so cannot create a
  * handle, but run their own descent loop and need the stop test.
- * Same draws, hit rule and result as knnd_fcc: idx (device, n x K int32),
- * samples S in [1, KNND_NOALLOC_MAX_SAMPLES] (EOVERFLOW above it), hits
- * (device int64, overwritten; -1 when a sampled friend index lies outside
- * [0, n)).  Enqueued on `stream` (cudaStream_t as void*).
+ * Same draws and hit rule as knnd_fcc: idx (device, n x K int32), samples S
+ * in [1, KNND_NOALLOC_MAX_SAMPLES] (EOVERFLOW above it), hits (device int64,
+ * overwritten).  On a graph whose indices all lie in [0, n) the count equals
+ * knnd_fcc's.  When a sampled friend index lies outside [0, n) the two
+ * differ: knnd_fcc counts that sample as a miss and records the bad index in
+ * the handle's sticky status (knnd_sync returns EINVAL), while this call
+ * writes -1 to hits.  Enqueued on `stream` (cudaStream_t as void*).
  * Scratch: a fixed array of about 32 KB in the library's device memory,
  * loaded with the library and held by every GPU that loads it until the
- * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  All calls on a device share the array:
- * calls that overlap on the GPU race.  Allocates nothing, frees nothing.
+ * process exits.  Every call looks up that array's device address in the
+ * current context (cudaGetSymbolAddress, with the device current; a host-side
+ * query, not a stream operation); the first call on a device also loads the
+ * library's device code there, so make that first call before any stream
+ * capture.  All calls on a device share the array, and each call clears its
+ * error word before sampling: calls that overlap on the GPU race.  Allocates
+ * nothing, frees nothing.
  * Errors: EINVAL (null pointer, shape as in knnd_create), EOVERFLOW, ECUDA. */
 knnd_status knnd_fcc_noalloc(const int32_t *idx, int64_t n, int32_t K, uint64_t seed, int32_t round,
                              int32_t samples, int64_t *hits, void *stream);
+
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11), the counter-based generator behind every random
+ * draw of this library: the uniform choices of the initial graph (Sec. 3.2)
+ * and of the clustering sample (Sec. 3.3) use counter (c0, c1, c2, block) and
+ * key (low and high 32 bits of the seed).  For i < count, out[4i .. 4i+3] =
+ * the ten-round Philox bijection of the counter ctr_key[6i .. 6i+3] under the
+ * key ctr_key[6i+4 .. 6i+5], computed by the same device routine the draws
+ * use; it exists so that this routine can be checked against the generator's
+ * published known-answer vectors.  ctr_key: device uint32, count x 6; out:
+ * device uint32, count x 4; enqueued on `stream` (cudaStream_t as void*).
+ * Errors: EINVAL (null pointer with count > 0, count < 0 or >= 2^31), ECUDA. */
+knnd_status knnd_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int64_t count, void *stream);
 
 /* Synchronise the handle's stream and return (and clear) the sticky device
  * status: EDOMAIN (bad coordinate), EINVAL (a graph index outside [0, n)

@@ -505,7 +505,10 @@ int32_t orc_build(const double *pts, int64_t n, int m, int K, uint64_t seed, int
 
 /* ------------------------------------------------------------------------ */
 /* Exact K-NN graph by brute force (Sec. 2.3): for each query x, the K best  */
-/* of S \ {x} under (key, index).                                           */
+/* of S \ {x} under (key, index).  Every y != x is keyed; a sorted list of   */
+/* the K best seen so far takes y when it ranks before the list's last      */
+/* entry, by insertion (the list a full sort of all n - 1 candidates would  */
+/* start with, without sorting them all).                                   */
 /* ------------------------------------------------------------------------ */
 void orc_bruteforce(const double *pts, int64_t n, int m, int K, const int32_t *queries, int64_t nq,
                     int32_t *idx, double *key)
@@ -515,18 +518,24 @@ void orc_bruteforce(const double *pts, int64_t n, int m, int K, const int32_t *q
     orc_tables(pts, n, m, L, negH);
 #pragma omp parallel
     {
-        orc_cand *c = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)n);
+        orc_cand *c = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)K);
 #pragma omp for schedule(dynamic, 4)
         for (int64_t q = 0; q < nq; ++q) {
             int64_t x = queries[q];
-            int64_t len = 0;
+            int len = 0; /* c[0 .. len) holds the best so far, sorted; len <= K */
             for (int64_t y = 0; y < n; ++y) {
                 if (y == x) continue;
-                c[len].idx = (int32_t)y;
-                c[len].key = orc_key_from_tables(pts, L, negH, m, x, y);
-                len += 1;
+                orc_cand e;
+                e.key = orc_key_from_tables(pts, L, negH, m, x, y);
+                e.idx = (int32_t)y;
+                if (len == K && orc_cand_cmp(&e, &c[K - 1]) >= 0) continue; /* not among the K best */
+                int t = len < K ? len++ : K - 1; /* a full list drops its last entry */
+                while (t > 0 && orc_cand_cmp(&e, &c[t - 1]) < 0) {
+                    c[t] = c[t - 1];
+                    --t;
+                }
+                c[t] = e;
             }
-            qsort(c, (size_t)len, sizeof(orc_cand), orc_cand_cmp);
             for (int t = 0; t < K; ++t) {
                 idx[q * K + t] = c[t].idx;
                 key[q * K + t] = c[t].key;

@@ -45,7 +45,7 @@ EXPORTS = [
     "knnd_create", "knnd_destroy", "knnd_set_stream", "knnd_prepare", "knnd_init_graph", "knnd_round",
     "knnd_fcc", "knnd_sync", "knnd_build", "knnd_build_host", "knnd_get_stats", "knnd_reset_stats",
     "knnd_status_string", "knnd_version", "knnd_fcc_noalloc", "knnd_batch_create", "knnd_batch_run",
-    "knnd_batch_info", "knnd_batch_destroy", "knnd_build_batched",
+    "knnd_batch_info", "knnd_batch_destroy", "knnd_build_batched", "knnd_philox4x32_10",
 ]
 
 KNND_NOALLOC_MAX_SAMPLES = 1 << 20
@@ -124,6 +124,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "knnd_batch_info": (i32, [P, P, P, P]),
         "knnd_batch_destroy": (None, [P]),
         "knnd_build_batched": (i32, [i32, P, i32, i32, ctypes.POINTER(knnd_params), i64, P, P]),
+        "knnd_philox4x32_10": (i32, [P, P, i64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -17,45 +17,32 @@
 // All calls on one device share it and it keeps the last call's contents, so
 // calls whose work overlaps on the GPU (different streams, or different host
 // threads, without ordering between them) race and may return wrong counts.
-#include <mutex>
-
 #include "knnd_internal.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = (KNND_NOALLOC_MAX_SAMPLES + kThreads - 1) / kThreads;
-constexpr int kMaxDevices = 64;
-
 // [0, 8): error word (int32) + pad; [256, 256 + 8 * kMaxBlocks): partial hit counts
 constexpr size_t kPartialsOffset = 256;
 constexpr size_t kScratchBytes = kPartialsOffset + sizeof(long long) * kMaxBlocks;
 
 static __device__ __align__(256) unsigned char g_fcc_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_fcc_scratch on the current device (looked up once per
-// device; in host code the symbol itself is only a host-side stand-in).
+// Device address of g_fcc_scratch in the current device's current context.
+// In host code the symbol itself is only a host-side stand-in.  The address is
+// looked up on every call (a host-side query, not a stream operation), never
+// cached: a context torn down and made again (cudaDeviceReset) reloads the
+// module, and an address kept from the old context would point nowhere.
 knnd_status scratch_address(void **out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_fcc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
         (void)cudaGetLastError();
         return KNND_ECUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_fcc_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            (void)cudaGetLastError();
-            return KNND_ECUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return KNND_OK;
 }
 

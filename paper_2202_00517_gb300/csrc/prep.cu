@@ -313,4 +313,27 @@ cudaError_t launch_fcc(knnd_handle *h, const int32_t *idx, uint64_t seed, int32_
     return cudaGetLastError();
 }
 
+// Raw Philox4x32-10 blocks: thread i maps counter ctr_key[6i..6i+3] under key
+// ctr_key[6i+4..6i+5] to out[4i..4i+3] with the routine every draw uses.
+__global__ void philox_kernel(const uint32_t *__restrict__ ck, uint32_t *__restrict__ out, int64_t count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint32_t *c = ck + 6 * i;
+    Philox ph(((uint64_t)c[5] << 32) | c[4], c[0], c[1], c[2]);
+    ph.block = c[3];
+    for (int w = 0; w < 4; ++w) out[4 * i + w] = ph.next();
+}
+
 }  // namespace knnd
+
+extern "C" knnd_status knnd_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int64_t count, void *stream)
+{
+    if (count < 0 || count >= ((int64_t)1 << 31)) return KNND_EINVAL;
+    if (count == 0) return KNND_OK;
+    if (!ctr_key || !out) return KNND_EINVAL;
+    const int threads = 128;
+    knnd::philox_kernel<<<(unsigned)((count + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(
+        ctr_key, out, count);
+    return cudaGetLastError() == cudaSuccess ? KNND_OK : KNND_ECUDA;
+}

@@ -22,7 +22,7 @@ def lib():
 def _declared():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(knnd_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(knnd_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declarations_are_exported(lib):
@@ -173,7 +173,7 @@ def test_missing_library_fails_loudly(monkeypatch):
 def test_binding_signatures_match_the_prototypes(lib):
     # each function the binding types takes as many arguments as its prototype
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
-    protos = dict(re.findall(r"\b(knnd_[a-z_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S))
+    protos = dict(re.findall(r"\b(knnd_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S))
     for name in _lib.EXPORTS:
         args = protos[name].strip()
         n = 0 if args in ("", "void") else args.count(",") + 1

@@ -1,0 +1,100 @@
+"""Parity at the high-dimension stress size: n = 4,000,000 Dirichlet(1) points on
+the 64-simplex (65 FP32 coordinates), K = 32, seed 2 -- the dimension range of
+Sec. 4.5, at the size the benchmark's second workload times.
+
+* The initial graph (Sec. 3.2) is compared with the oracle's in full.
+* Every round of the build (mixed form, rounds launched one by one) is checked
+  in lockstep: the CUDA round starts from the CUDA graph G_{r-1}, the oracle
+  computes G_r's rows on sampled ranges from the same graph (Sec. 3.1,
+  Sec. 4.2), and the two are compared under the tie rule, with those rows'
+  new-flags, the full clustering hit counts (Sec. 3.3) and the stop round.
+* The three forms (FP64; FP32 filter; BF16 hi/lo tensor-core tiles) build the
+  same graph bit for bit, and that graph equals the lockstep graph.
+* Rounds stay within twice a lower bound of diam(G0) (Sec. 3.2, Sec. 4.3), and
+  recall against brute force on 1,000 evenly spaced queries is reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_00517_gb300.datagen import dirichlet_points
+from parity_util import check_invariants, compare_graphs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+N, M, K, SEED = 4_000_000, 65, 32, 2
+
+
+@pytest.fixture(scope="module")
+def data():
+    assert torch.cuda.is_available()
+    import paper_2202_00517_gb300 as knnd
+    pts = dirichlet_points(N, M, SEED, np.float32)
+    pts64 = pts.astype(np.float64)
+    g0i, g0k = oracle.init_graph(pts64, K, SEED)
+    return knnd, pts, pts64, g0i, g0k
+
+
+def test_config4_lockstep_and_forms(data):
+    knnd, pts, pts64, g0i, g0k = data
+    p = torch.from_numpy(pts).cuda()
+    S = 10_000
+    ranges = [(0, 1500), (N // 2, N // 2 + 1000), (N - 1500, N)]
+    h = knnd.Handle(N, M, K, dtype="f32", precision="mixed", fcc_samples=S)
+    idx, key, flag = h.init_graph(p, SEED)
+    gi = idx.cpu().numpy()
+    assert np.array_equal(gi, g0i)
+    compare_graphs(pts64, gi, key.cpu().numpy(), g0i, g0k, rows=np.arange(0, N, 3989), max_tie_rows=0)
+    upd = torch.zeros(1, dtype=torch.int64, device="cuda")
+    hits = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h.fcc(idx, SEED, 0, hits)
+    h.sync()
+    prev_hits = oracle.fcc(g0i, SEED, 0, S)
+    assert int(hits.item()) == prev_hits
+    r, ties, stop = 0, 0, None
+    while stop is None:
+        r += 1
+        prev = idx.cpu().numpy()
+        h.round(None, SEED, r, idx, key, flag, upd, hits)
+        h.sync()
+        gi, gk, gf = idx.cpu().numpy(), key.cpu().numpy(), flag.cpu().numpy()
+        for x0, x1 in ranges:
+            ri, rk, rf, _, _ = oracle.round_(pts64, prev, x0, x1)
+            ties += compare_graphs(pts64, gi, gk, ri, rk, rows=np.arange(x0, x1))
+            same = np.all(gi[x0:x1] == ri[x0:x1], axis=1)
+            assert np.array_equal(gf[x0:x1][same], rf[x0:x1][same]), r
+        assert int(upd.item()) == int(gf.sum())
+        h_r = oracle.fcc(gi, SEED, r, S)
+        assert int(hits.item()) == h_r, (r, int(hits.item()), h_r)
+        if h_r <= prev_hits:
+            stop = 1
+        elif int(upd.item()) == 0:
+            stop = 2
+        prev_hits = h_r
+    print(f"config 4 lockstep rounds={r} near-tie rows={ties}")
+    assert ties <= 3 * r
+    check_invariants(gi, gk)
+    h.close()
+    del prev, gf
+    builds = {}
+    for prec in ("mixed", "bf16x3", "fp64"):
+        hb = knnd.Handle(N, M, K, dtype="f32", precision=prec, fcc_samples=S)
+        b = hb.build(p, SEED)
+        hb.close()
+        builds[prec] = b
+        assert b["rounds"] == r and b["stop_reason"] == stop, prec
+        assert torch.equal(b["idx"], idx) and torch.equal(b["key"], key), prec
+        print(f"{prec}: rounds={b['rounds']} rescored={b['rescored']} survivors={b['join_survivors']}")
+        del b["idx"], b["key"], b["flag"]
+    a = builds["fp64"]
+    for prec in ("mixed", "bf16x3"):
+        assert builds[prec]["updates"] == a["updates"] and builds[prec]["fcc_hits"] == a["fcc_hits"], prec
+    lo, hi = oracle.diameter_bounds(g0i, sweeps=2, seed=SEED)
+    assert lo > 0 and r <= 2 * lo, (r, lo, hi)
+    q = np.linspace(0, N - 1, 1_000).astype(np.int32)
+    bi, _ = oracle.bruteforce(pts64, K, q)
+    recall = float(np.mean([len(set(bi[t]) & set(gi[x])) / K for t, x in enumerate(q)]))
+    print(f"config 4: rounds={r} diam(G0) in [{lo}, {hi}] recall@{K}={recall:.3f} (1,000 queries)")
+    assert recall > 0.2

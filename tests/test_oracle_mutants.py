@@ -35,6 +35,12 @@ MUTANTS = [
      "uint64_t p0 = (uint64_t)ORC_PH_M1 * (uint64_t)c0;"),
     ("philox_nine_rounds", "for (int r = 0; r < 10; ++r) {", "for (int r = 0; r < 9; ++r) {"),
     ("philox_key_bump_dropped", "k1 += ORC_PH_W1;", "k1 += 0u;"),
+    ("philox_output_words_swapped", "out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;",
+     "out[0] = c1; out[1] = c0; out[2] = c2; out[3] = c3;"),
+    ("philox_key_bumped_before_round",
+     "        uint32_t n0 = hi1 ^ c1 ^ k0;\n        uint32_t n1 = lo1;\n        uint32_t n2 = hi0 ^ c3 ^ k1;",
+     "        k0 += ORC_PH_W0;\n        k1 += ORC_PH_W1;\n        uint32_t n0 = hi1 ^ c1 ^ k0;\n"
+     "        uint32_t n1 = lo1;\n        uint32_t n2 = hi0 ^ c3 ^ k1;\n        k0 -= ORC_PH_W0;\n        k1 -= ORC_PH_W1;"),
     ("lemire_low_half", "return (uint32_t)(mprod >> 32);", "return (uint32_t)mprod % N;"),
     ("lemire_no_rejection", "while (low < thresh) {", "while (0 && low < thresh) {"),
     ("negH_term_dropped", "acc = fma(pts[y * m + i], l, acc);", "acc = l + acc;"),
@@ -88,9 +94,10 @@ MUTANTS = [
     ("inner_offset_one", "            off[y] = 0.0;", "            off[y] = 1.0;"),
     ("fcc_i_range_short", "int i = (int)orc_bounded(&st, (uint32_t)K);", "int i = (int)orc_bounded(&st, (uint32_t)(K - 1));"),
     ("fcc_x_range_short", "int64_t x = orc_bounded(&st, (uint32_t)n);", "int64_t x = orc_bounded(&st, (uint32_t)(n / 2));"),
-    ("bruteforce_partial_sort",
-     "qsort(c, (size_t)len, sizeof(orc_cand), orc_cand_cmp);\n            for (int t = 0; t < K; ++t) {\n                idx[q * K + t]",
-     "qsort(c, (size_t)(len / 2), sizeof(orc_cand), orc_cand_cmp);\n            for (int t = 0; t < K; ++t) {\n                idx[q * K + t]"),
+    ("bruteforce_never_first", "while (t > 0 && orc_cand_cmp(&e, &c[t - 1]) < 0) {",
+     "while (t > 1 && orc_cand_cmp(&e, &c[t - 1]) < 0) {"),
+    ("bruteforce_keeps_first_k", "if (len == K && orc_cand_cmp(&e, &c[K - 1]) >= 0) continue;",
+     "if (len == K) continue;"),
     ("bfs_disconnected_ignored", "return tail == n ? ecc : -1;", "return ecc;"),
     ("diameter_lower_from_first_sweep_only", "if (e > best_lo) best_lo = e;", "if (t == 0 && e > best_lo) best_lo = e;"),
 ]

@@ -92,3 +92,32 @@ def test_bounded_unbiased_where_truncation_is_worst():
     d = oracle.bounded_draws(5, 0, 0, 0, N, 40_000).astype(np.int64)
     assert d.max() < N
     assert abs(np.mean(d % 2 == 0) - 0.5) < 0.015
+
+
+def test_oracle_philox_known_answers():
+    """The published Philox4x32-10 known-answer vectors (tests/golden): a swapped
+    output word, a key bumped before the first round or a wrong multiplier all
+    fail here."""
+    from kat import philox_kat
+    rows = philox_kat()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        assert np.array_equal(oracle.philox4x32_10(ctr, key), want), (ctr, key)
+
+
+def test_input_generator_philox_known_answers():
+    from kat import philox_kat
+    for ctr, key, want in philox_kat():
+        seed = (int(key[1]) << 32) | int(key[0])
+        got = datagen._philox_blocks(np.array([ctr[0]], dtype=np.uint64), int(ctr[1]), int(ctr[2]), int(ctr[3]),
+                                     seed)[0]
+        assert np.array_equal(got, want), (ctr, key)
+
+
+def test_stream_words_follow_the_known_answers():
+    """The oracle's word stream (seed, c0, c1, c2) starts with block c3 = 0: the
+    all-zero vector is the first four words of stream (0, 0, 0, 0)."""
+    from kat import philox_kat
+    ctr, key, want = philox_kat()[0]
+    assert not ctr.any() and not key.any()
+    assert np.array_equal(oracle.stream_words(0, 0, 0, 0, 4), want)

@@ -74,3 +74,33 @@ def test_noalloc_fcc_limits():
     torch.cuda.synchronize()
     # consecutive generators: every pair of friends is linked, so every sample hits
     assert int(out.item()) == S
+
+
+def test_noalloc_fcc_bad_index_then_valid_graph():
+    """A graph holding indices outside [0, n) gives hits = -1 (the kernel checks
+    an index before following it, so nothing is read out of bounds); the error
+    word lives in the shared scratch array, so the next call on a valid graph
+    must clear it and return the handle's count again."""
+    import paper_2202_00517_gb300 as knnd
+    from paper_2202_00517_gb300 import _lib
+    lib = _lib.load()
+    n, K, seed, S = 1_000, 8, 5, 10_000
+    ring = ((torch.arange(n, device="cuda")[:, None] + torch.arange(1, K + 1, device="cuda")[None, :]) % n)
+    ring = ring.to(torch.int32).contiguous()
+    bad = ring.clone()
+    bad[0::2, :] = n        # every even row: only the index n, one past the last point
+    bad[1::4, 0] = -1       # and some odd rows start with -1
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        out.fill_(123)
+        assert _noalloc(lib, bad, seed, 3, S, out) == _lib.KNND_OK
+        torch.cuda.synchronize()
+        assert int(out.item()) == -1
+    h = knnd.Handle(n, 4, K, dtype="f32", precision="mixed", fcc_samples=S)
+    ref = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h.fcc(ring, seed, 3, ref)
+    h.sync()
+    assert _noalloc(lib, ring, seed, 3, S, out) == _lib.KNND_OK
+    torch.cuda.synchronize()
+    assert int(out.item()) == int(ref.item()) == S  # consecutive generators: every sample hits
+    h.close()
