@@ -97,4 +97,4 @@ def test_config4_lockstep_and_forms(data):
     bi, _ = oracle.bruteforce(pts64, K, q)
     recall = float(np.mean([len(set(bi[t]) & set(gi[x])) / K for t, x in enumerate(q)]))
     print(f"config 4: rounds={r} diam(G0) in [{lo}, {hi}] recall@{K}={recall:.3f} (1,000 queries)")
-    assert recall > 0.2
+    assert recall > 0.22  # measured 0.287 on GB300 (1,000 queries)

@@ -93,7 +93,7 @@ def test_full_builds(data):
     bi, _ = oracle.bruteforce(pts64, K, q)
     recall = float(np.mean([len(set(bi[t]) & set(idx[x])) / K for t, x in enumerate(q)]))
     print(f"rounds={r} updates={b['updates']} fcc={h} recall@{K}={recall:.3f} rescored={b['rescored']}")
-    assert recall > 0.5
+    assert recall > 0.6  # measured 0.680 on GB300 (10,000 queries)
 
 
 def test_every_round_lockstep_sampled(data):
