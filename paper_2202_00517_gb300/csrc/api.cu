@@ -435,6 +435,7 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
         return KNND_ECUDA;
     }
     if (const char *f = std::getenv("KNND_TEST_FAIL_ALLOC")) h->fail_alloc_at = std::atoi(f);
+    if (const char *j = std::getenv("KNND_JOIN")) h->join_lsu = std::strcmp(j, "lsu") == 0 ? 1 : 0;
     const int64_t n = c.n;
     knnd_status s = KNND_OK;
     const int64_t ntiles = (n + 2047) / 2048;

@@ -759,6 +759,11 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_
 {
     if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && h->prm.comparator == KNND_CMP_KL)
         return launch_join_tc(h, idx, h_lo, h_hi, phase, split_den);
+    if (!h->join_lsu && tma_join_supported(h)) {
+        cudaMemsetAsync(h->bcnt, 0, sizeof(int32_t) * h->n, h->stream);
+        h->launches += 1;
+        return launch_join_tma(h, idx, h_lo, h_hi, phase, split_den);
+    }
     JoinArgs a;
     a.n = h->n;
     a.h_lo = h_lo;

@@ -1,0 +1,616 @@
+// join_tma.cu -- the FP32 filter of the local join (Sec. 3.1 "Meet", Sec. 4.2)
+// with its rows and columns brought into shared memory by the TMA engine.
+//
+// Same hub tiles, filter, bucket entries and error bound as join_mixed_kernel
+// (join.cu): hub v's rows are F(v) then coF(v), its columns F(v) and, for the
+// rows of F(v), v itself; a pair is kept when its FP32 dot can still beat the
+// row's K-th entry.  What differs is how the tile reaches the FP32 pipe:
+//
+//  * a warp takes a hub's rows 32 at a time (an item); lane t owns row t of the
+//    item for the whole item: its coordinates sit in registers, so the dots of
+//    a row are finished in the lane that filters them and never pass through
+//    shared memory;
+//  * the 32 rows of an item and the K + 1 columns of a hub are gathered from
+//    the FP32 tables by cp.async.bulk.tensor ... tile::gather4 (four indexed
+//    rows of a two-dimensional tensor map per instruction, one row high), which
+//    moves them into shared memory without passing through the load/store
+//    pipe; an index outside the table (an empty row slot) reads zeros;
+//  * the copies of the next item are issued as soon as the current item's rows
+//    have left the staging buffer, and the ids of the item after it are loaded
+//    while the current item is scored, so gathers, id chases and scoring of
+//    three consecutive items overlap within one warp;
+//  * every lane reads each column coordinate from shared memory as a broadcast
+//    (all lanes, one address) and uses it in one fma of its own row.
+//
+// Each dot is two fma chains, one over the even and one over the odd
+// coordinates, run together by packed two-wide FP32 fmas (__ffma2_rn, one
+// instruction for both), then added: at most ceil(m/2) + 1 roundings on any
+// term, within the m + 6 that the filter's bound c_m = (m + 6) 2^-24 (1.01)
+// allows for (Higham, Sec. 3.1: the bound holds for any summation order).  debug = 1 audits every dot against FP64 for
+// the comparators whose bound is E_x itself.  Incremental proposals and the
+// inner product's heavy-hub pass stay with join.cu.
+//
+// Every mbarrier wait is bounded (1 s of the global timer); on a timeout the
+// warp sets kErrTimeout, waits (bounded) for its copies in flight and stops.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "knnd_internal.cuh"
+
+namespace knnd {
+
+struct TmaJoinArgs {
+    CUtensorMap tm_row;  // the rows' FP32 table (X32; reverse KL: L32), n x MP, box MP x 1
+    CUtensorMap tm_col;  // the columns' FP32 table (L32; reverse KL: X32)
+    int64_t n;
+    int64_t h_lo, h_hi;  // hubs [h_lo, h_hi) of phase `phase` (in_phase)
+    int phase, split_den;
+    int K, MP;
+    const int32_t *idx;
+    const int64_t *cof_off;
+    const int32_t *cof;
+    const RowMeta *meta;
+    const double *negH;  // column offsets (comparators with one)
+    int32_t *bcnt;
+    int2 *bent;
+    int32_t *err;
+    int debug;
+    InstView iv;
+    float col_scale;
+    double col_inv;
+    // bound audit (debug, comparators without a column offset): the FP64
+    // tables, the bound of each row and the counters it adds to
+    const double *X64;
+    const double *L64;
+    const double *Ex;
+    int64_t *cnt;
+};
+
+namespace {
+
+constexpr unsigned long long kTmaWaitNs = 1000000000ull;  // 1 s
+constexpr int kSlot = 36;  // column ids per slot: K + 1 <= 33, padded
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Polls phase `parity` of the mbarrier until it completes (true) or `limit` ns pass (false).
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, unsigned long long limit)
+{
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (it == 0) t0 = now_ns();
+        else if ((it & 31) == 0 && now_ns() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void expect_bytes(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Four rows r0..r3 (all MP coordinates) of the tensor map's table -> 4 x MP
+// floats at dst; an out-of-range row index reads zeros.
+__device__ __forceinline__ void gather4(uint32_t dst, const CUtensorMap *tm, int r0, int r1, int r2, int r3,
+                                        uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(tm), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+        : "memory");
+}
+
+// Per-warp shared memory (bytes).  KC: column rows staged, K + 1 rounded up to 4;
+// column ids (and, with a column offset, RD(co(y)/s)) in two slots of 36.
+struct TmaLayout {
+    int MP, K, KC, SVS;
+    int off_row, off_col0, off_col1, off_sv, off_cid, off_h, off_inc, off_rb, off_mask, off_bar, bytes;
+    __host__ __device__ TmaLayout(int mp, int k, bool col) : MP(mp), K(k)
+    {
+        KC = (K + 1 + 3) & ~3;
+        SVS = K + 1;                          // survivor slots of a row
+        const int rowb = 32 * MP * 4;         // a multiple of 128 (MP a multiple of 8)
+        const int colb = (KC * MP * 4 + 127) & ~127;
+        off_row = 0;
+        off_col0 = off_row + rowb;
+        off_col1 = off_col0 + colb;
+        off_sv = off_col1 + colb;
+        off_cid = off_sv + ((32 * SVS * 4 + 15) & ~15);
+        off_h = off_cid + 2 * kSlot * 4;
+        off_inc = off_h + (col ? 2 * kSlot * 4 : 0);
+        off_rb = off_inc + 32 * 4;
+        off_mask = off_rb + 32 * 8;
+        off_bar = off_mask + 32 * 4;
+        bytes = (off_bar + 3 * 8 + 127) & ~127;
+    }
+};
+
+// The warp's current position in its hubs: hub v, its item `ch` (rows
+// 32 ch .. 32 ch + 31), the start of coF(v) and the hub's row count.
+struct Item {
+    int64_t v;
+    int64_t c0;
+    int nrows;
+    int ch;
+    bool valid;
+};
+
+// The warp's walk over its hubs h_lo + first, + stride, ...: the next hub to
+// consider and its co-friend offsets, loaded one hub ahead of their use.
+struct HubWalk {
+    int64_t next;
+    int64_t c0, c1;  // cof_off[next], cof_off[next + 1] (when next < h_hi)
+};
+
+__device__ __forceinline__ void walk_load(const TmaJoinArgs &a, HubWalk &w)
+{
+    if (w.next < a.h_hi) {
+        w.c0 = a.cof_off[w.next];
+        w.c1 = a.cof_off[w.next + 1];
+    }
+}
+
+// The item after `it`: the hub's next 32 rows, or the first rows of the
+// warp's next hub that is live and in the launch's phase.
+__device__ __forceinline__ Item next_item(const TmaJoinArgs &a, Item it, HubWalk &w, int64_t stride)
+{
+    if (it.valid && (it.ch + 1) * 32 < it.nrows) {
+        it.ch += 1;
+        return it;
+    }
+    Item r;
+    r.valid = false;
+    r.v = r.c0 = 0;
+    r.nrows = r.ch = 0;
+    while (w.next < a.h_hi) {
+        const int64_t v = w.next;
+        if (!a.iv.live(v) || !in_phase(a.iv, a.phase, a.split_den, a.n, v)) {
+            w.next += stride;
+            walk_load(a, w);
+            continue;
+        }
+        r.v = v;
+        r.c0 = w.c0;
+        r.nrows = a.K + (int)(w.c1 - w.c0);
+        r.valid = true;
+        w.next += stride;
+        walk_load(a, w);  // in flight until the warp's next hub
+        break;
+    }
+    return r;
+}
+
+// Bound audit (debug): the FP32 dot d of row x and column y against the FP64
+// dot of the same tables; a difference above the row's bound E_x counts as a
+// violation (the filter relies on there being none).
+__device__ __noinline__ void audit_pair(const TmaJoinArgs &a, int x, int y, float d, long long &ndot,
+                                        long long &nviol)
+{
+    const int MP = a.MP;
+    const double *xr = a.X64 + (int64_t)x * MP;
+    const double *lr = a.L64 + (int64_t)y * MP;
+    double acc = 0.0;
+    for (int i = 0; i < MP; ++i) acc = __fma_rn(xr[i], lr[i], acc);
+    ndot += 1;
+    if (fabs((double)d - acc) > a.Ex[x]) nviol += 1;
+}
+
+// Lane `lane`'s row of item `it` as stored (-1: no row).  Not yet checked, so
+// that the load stays in flight until check_id.
+__device__ __forceinline__ int load_id(const TmaJoinArgs &a, const Item &it, int lane)
+{
+    if (!it.valid) return -1;
+    const int r = it.ch * 32 + lane;
+    if (r >= it.nrows) return -1;
+    return r < a.K ? a.idx[it.v * a.K + r] : a.cof[it.c0 + (r - a.K)];
+}
+
+// An index outside [0, n) is recorded in the error word and skipped (-1).
+__device__ __forceinline__ int check_id(const TmaJoinArgs &a, int id, bool present)
+{
+    if (present && (id < 0 || (int64_t)id >= a.n)) {
+        atomicOr(a.err, kErrIndex);
+        return -1;
+    }
+    return present ? id : -1;
+}
+
+__device__ __forceinline__ bool has_row(const Item &it, int lane)
+{
+    return it.valid && it.ch * 32 + lane < it.nrows;
+}
+
+}  // namespace
+
+// AUDIT: the debug form (debug = 1) of a comparator without a column offset,
+// compiled apart so that the default form carries none of its state.
+template <int MP, bool COL, bool AUDIT>
+__global__ void __launch_bounds__(128, MP <= 24 ? 5 : 4) join_tma_kernel(const __grid_constant__ TmaJoinArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int K = a.K;
+    const TmaLayout L(MP, K, COL);
+    long long ndot = 0, nviol = 0;
+    unsigned char *wb = smem_tma + (size_t)warp * L.bytes;
+    const float *sRow = reinterpret_cast<const float *>(wb + L.off_row);
+    float *sSv = reinterpret_cast<float *>(wb + L.off_sv);     // [32][SVS] survivor dots of each row
+    unsigned *sMask = reinterpret_cast<unsigned *>(wb + L.off_mask);  // columns that passed, per row
+    int *sCid = reinterpret_cast<int *>(wb + L.off_cid);       // [2][kSlot] column ids per slot
+    float *sH = reinterpret_cast<float *>(wb + L.off_h);        // [2][kSlot] RD(co(y) / s) per slot (COL)
+    int *sInc = reinterpret_cast<int *>(wb + L.off_inc);
+    long long *sRB = reinterpret_cast<long long *>(wb + L.off_rb);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(wb + L.off_bar);
+    const uint32_t row_dst = saddr(wb + L.off_row);
+    const uint32_t col_dst0 = saddr(wb + L.off_col0), col_step = (uint32_t)(L.off_col1 - L.off_col0);
+    const uint32_t bar_row = saddr(bars), bar_col0 = bar_row + 8u;  // slot s: bar_col0 + 8 s
+    const uint32_t row_bytes = 32u * MP * 4u, col_bytes = (uint32_t)L.KC * MP * 4u;
+    if (saddr(smem_tma) & 127u) {  // the copies need 128-byte aligned destinations (reported as a failed wait)
+        if (lane == 0) atomicOr(a.err, kErrTimeout);
+        return;
+    }
+    if (lane == 0) {
+        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bars + b)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncwarp();
+
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    HubWalk walk;
+    walk.next = a.h_lo + (int64_t)blockIdx.x * wpb + warp;
+    walk.c0 = walk.c1 = 0;
+    walk_load(a, walk);
+    Item none;
+    none.valid = false;
+    none.v = none.c0 = 0;
+    none.nrows = none.ch = 0;
+
+    // Copies of item `it` (lane ids `rid`): its 32 rows; with its hub's first
+    // item, the hub's columns into column slot `slot`, their ids into sCid.
+    auto issue = [&](const Item &it, int rid, int slot) {
+        const bool cols = it.ch == 0;
+        if (cols) {
+            if (lane < K) sCid[slot * kSlot + lane] = rid;
+            if (lane == 0) sCid[slot * kSlot + K] = (int)it.v;
+            if (COL) {
+                if (lane < K) sH[slot * kSlot + lane] = rid >= 0 ? __double2float_rd(a.negH[rid] * a.col_inv) : 0.f;
+                if (lane == 0) sH[slot * kSlot + K] = __double2float_rd(a.negH[it.v] * a.col_inv);
+            }
+        }
+        // gather coordinates: lanes 0..7 take rows 4l..4l+3, lanes 8..8+KC/4-1 columns 4(l-8)..
+        const int g = lane < 8 ? lane : lane - 8;
+        int q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int src = (4 * g + i) & 31;
+            const int v = __shfl_sync(FULL, rid, src);
+            q[i] = v;
+            if (lane >= 8) {
+                const int c = 4 * g + i;
+                q[i] = c < K ? v : (c == K ? (int)it.v : -1);
+            }
+        }
+        __syncwarp();  // every lane's reads of the staging buffer come before the copies below
+        if (lane == 0) {
+            expect_bytes(bar_row, row_bytes);
+            if (cols) expect_bytes(bar_col0 + 8u * slot, col_bytes);
+        }
+        __syncwarp();
+        if (lane < 8) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            gather4(row_dst + (uint32_t)(lane * 4 * MP * 4), &a.tm_row, q[0], q[1], q[2], q[3], bar_row);
+        } else if (cols && lane < 8 + L.KC / 4) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            gather4(col_dst0 + col_step * slot + (uint32_t)((lane - 8) * 4 * MP * 4), &a.tm_col, q[0], q[1], q[2],
+                    q[3], bar_col0 + 8u * slot);
+        }
+    };
+
+    // prologue: item A's copies in flight, item B's ids loading
+    Item A = next_item(a, none, walk, stride);
+    if (!A.valid) return;
+    int ridA = check_id(a, load_id(a, A, lane), has_row(A, lane));
+    Item B = next_item(a, A, walk, stride);
+    int ridB = load_id(a, B, lane);
+    int slotA = 0;
+    issue(A, ridA, slotA);
+    RowMeta mA;
+    mA.phi = 0.f;
+    mA.boff = 0;
+    if (ridA >= 0) mA = a.meta[ridA];
+    uint32_t prow = 0, pcol = 0;  // phase parities: the row barrier; bit s, column slot s
+
+    while (A.valid) {
+        // 1. item A's rows: wait, then this lane's row into registers
+        if (!wait_phase(bar_row, prow, kTmaWaitNs)) {
+            atomicOr(a.err, kErrTimeout);
+            wait_phase(bar_row, prow, kTmaWaitNs);
+            if (A.ch == 0) wait_phase(bar_col0 + 8u * slotA, (pcol >> slotA) & 1u, kTmaWaitNs);
+            return;
+        }
+        prow ^= 1u;
+        float2 x[MP / 2];  // coordinates (2i, 2i + 1) of this lane's row
+        {
+            const float4 *xr = reinterpret_cast<const float4 *>(sRow + lane * MP);
+#pragma unroll
+            for (int i4 = 0; i4 < MP / 4; ++i4) {
+                const float4 t = xr[i4];
+                x[2 * i4 + 0] = make_float2(t.x, t.y);
+                x[2 * i4 + 1] = make_float2(t.z, t.w);
+            }
+        }
+        __syncwarp();
+        // 2. item B's copies (the staging buffer is free again)
+        const int slotB = (B.valid && B.ch == 0) ? slotA ^ 1 : slotA;
+        ridB = check_id(a, ridB, has_row(B, lane));
+        if (B.valid) issue(B, ridB, slotB);
+        // 3. item C's ids and item B's row records, in flight while A is scored
+        const Item C = next_item(a, B, walk, stride);
+        const int ridC = load_id(a, C, lane);
+        RowMeta mB;
+        mB.phi = 0.f;
+        mB.boff = 0;
+        if (ridB >= 0) mB = a.meta[ridB];
+        // 4. item A's columns (first item of its hub)
+        if (A.ch == 0) {
+            if (!wait_phase(bar_col0 + 8u * slotA, (pcol >> slotA) & 1u, kTmaWaitNs)) {
+                atomicOr(a.err, kErrTimeout);
+                wait_phase(bar_col0 + 8u * slotA, (pcol >> slotA) & 1u, kTmaWaitNs);
+                if (B.valid) {
+                    wait_phase(bar_row, prow, kTmaWaitNs);
+                    if (B.ch == 0) wait_phase(bar_col0 + 8u * slotB, (pcol >> slotB) & 1u, kTmaWaitNs);
+                }
+                return;
+            }
+            pcol ^= 1u << slotA;
+        }
+        // 5. score row ridA against the hub's columns, filter, compact
+        const float4 *Cb = reinterpret_cast<const float4 *>(wb + (slotA ? L.off_col1 : L.off_col0));
+        const int *cid = sCid + slotA * kSlot;
+        const float *hcol = sH + slotA * kSlot;
+        const float ph = mA.phi;
+        float *sv = sSv + lane * L.SVS;
+        int q = 0;
+        unsigned mk = 0u;  // bit j: column j passed
+        for (int j0 = 0; j0 < K; j0 += 4) {
+            // column j0 + k: chains over the even and the odd coordinates
+            float2 e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[k] = make_float2(0.f, 0.f);
+            const float4 *c0 = Cb + j0 * (MP / 4);
+#pragma unroll
+            for (int i4 = 0; i4 < MP / 4; ++i4) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float4 u = c0[k * (MP / 4) + i4];
+                    e[k] = __ffma2_rn(x[2 * i4], make_float2(u.x, u.y), e[k]);
+                    e[k] = __ffma2_rn(x[2 * i4 + 1], make_float2(u.z, u.w), e[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = j0 + k;
+                const float d = __fadd_rn(e[k].x, e[k].y);
+                const int cj = cid[j];  // j < K + 3 < 2 kSlot: inside the slot pair
+                const bool pair = j < K && ridA >= 0 && cj >= 0 && cj != ridA;
+                if (AUDIT && pair) audit_pair(a, ridA, cj, d, ndot, nviol);
+                const float thr = COL ? __fsub_rd(hcol[j], ph) : ph;
+                const bool pass = pair && d >= thr;
+                if (pass) sv[q] = d;
+                q += pass ? 1 : 0;
+                mk |= (pass ? 1u : 0u) << j;
+            }
+        }
+        // the co-friend pair (x in F(v), y = v): column K, rows of F(v) only
+        if (A.ch == 0) {
+            const float4 *cv = Cb + K * (MP / 4);
+            float2 e = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i4 = 0; i4 < MP / 4; ++i4) {
+                const float4 u = cv[i4];
+                e = __ffma2_rn(x[2 * i4], make_float2(u.x, u.y), e);
+                e = __ffma2_rn(x[2 * i4 + 1], make_float2(u.z, u.w), e);
+            }
+            const float acc = __fadd_rn(e.x, e.y);
+            if (lane < K && ridA >= 0) {
+                if (AUDIT) audit_pair(a, ridA, (int)A.v, acc, ndot, nviol);
+                const float hv = COL ? hcol[K] : 0.f;
+                if (acc >= (COL ? __fsub_rd(hv, ph) : ph)) {
+                    sv[q] = acc;  // the last survivor of the row
+                    ++q;
+                }
+            }
+        }
+        // 6. reserve the row's bucket slots, then write the item's survivors
+        //    coalesced: entry k of the flattened list belongs to the first lane
+        //    whose inclusive prefix exceeds k
+        long long rowbase = -1;
+        if (q > 0) {
+            const int p = atomicAdd(&a.bcnt[ridA], q);
+            rowbase = mA.boff + p;
+            if (a.debug) {
+                const int64_t cap =
+                    (int64_t)K * K + (int64_t)(K + 1) * (a.cof_off[ridA + 1] - a.cof_off[ridA]);
+                if (p + q > cap) {
+                    atomicOr(a.err, kErrBucket);
+                    rowbase = -1;
+                }
+            }
+        }
+        int incl = q;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        sInc[lane] = incl;
+        sRB[lane] = rowbase;
+        sMask[lane] = mk;
+        __syncwarp();
+        for (int k = lane; k < total; k += 32) {
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int it = 0; it < 5; ++it) {
+                const int mid = (lo + hi) >> 1;
+                if (sInc[mid] > k) hi = mid;
+                else lo = mid + 1;
+            }
+            const int t = lo;
+            const int qq = k - (t ? sInc[t - 1] : 0);
+            const long long rb = sRB[t];
+            if (rb >= 0) {
+                // survivor qq of row t: its qq-th passing column, or (past them) the hub itself
+                const float d = sSv[t * L.SVS + qq];
+                const bool colj = qq < __popc(sMask[t]);
+                const int j = colj ? (int)__fns(sMask[t], 0, qq + 1) : K;
+                const int y = colj ? cid[j] : (int)A.v;
+                // the entry orders the candidates like their keys: -d, or s (co(y)/s - d)
+                a.bent[rb + qq] =
+                    make_int2((int)sortable_bits(COL ? __fmul_rn(a.col_scale, __fsub_rn(hcol[j], d)) : -d), y);
+            }
+        }
+        __syncwarp();
+        // 7. advance
+        A = B;
+        ridA = ridB;
+        mA = mB;
+        slotA = slotB;
+        B = C;
+        ridB = ridC;
+    }
+    if (AUDIT) {
+        for (int o = 16; o > 0; o >>= 1) {
+            ndot += __shfl_xor_sync(FULL, ndot, o);
+            nviol += __shfl_xor_sync(FULL, nviol, o);
+        }
+        if (lane == 0) {
+            atomicAdd((unsigned long long *)&a.cnt[kCntAudited], (unsigned long long)ndot);
+            if (nviol) atomicAdd((unsigned long long *)&a.cnt[kCntBoundViol], (unsigned long long)nviol);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+// A two-dimensional map of an n x MP FP32 table whose box is one whole row
+// (the form tile::gather4 takes); rows outside [0, n) read zeros.
+bool row_map(CUtensorMap *m, const float *table, int64_t n, int MP)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)MP, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)MP * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)MP, 1u};
+    const cuuint32_t es[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(table), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MP, bool COL>
+cudaError_t run_tma(knnd_handle *h, const TmaJoinArgs &a)
+{
+    const int threads = 128;
+    const TmaLayout L(MP, h->K, COL);
+    const size_t smem = (size_t)L.bytes * (threads / 32);
+    auto kern = (!COL && a.debug) ? join_tma_kernel<MP, COL, !COL> : join_tma_kernel<MP, COL, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t need = (a.h_hi - a.h_lo + threads / 32 - 1) / (threads / 32);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)h->num_sms * per_sm));
+    kern<<<(unsigned)grid, threads, smem, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tma_join_supported(const knnd_handle *h)
+{
+    return h->prec != KNND_PREC_FP64 && h->round_flag == nullptr && h->prm.comparator != KNND_CMP_INNER &&
+           h->K <= 32 && h->MP <= 32 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_join_tma(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase,
+                            int split_den)
+{
+    TmaJoinArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const int cmp = h->prm.comparator;
+    const float *rows = h->X32, *cols = h->L32;
+    if (cmp == KNND_CMP_KL_REVERSE) std::swap(rows, cols);  // rows read log x, columns read y
+    if (!row_map(&a.tm_row, rows, h->n, h->MP) || !row_map(&a.tm_col, cols, h->n, h->MP))
+        return cudaErrorInvalidValue;
+    a.n = h->n;
+    a.h_lo = h_lo;
+    a.h_hi = h_hi;
+    a.phase = phase;
+    a.split_den = split_den;
+    a.K = h->K;
+    a.MP = h->MP;
+    a.idx = idx;
+    a.cof_off = h->cof_off;
+    a.cof = h->cof;
+    a.meta = h->meta;
+    a.negH = h->negH;
+    a.bcnt = h->bcnt;
+    a.bent = h->bent;
+    a.err = h->err;
+    a.debug = h->prm.debug;
+    a.iv = h->iv;
+    a.col_scale = cmp == KNND_CMP_SQEUCLIDEAN ? 2.f : 1.f;
+    a.col_inv = cmp == KNND_CMP_SQEUCLIDEAN ? 0.5 : 1.0;
+    a.X64 = h->X64;
+    a.L64 = h->L64;
+    a.Ex = h->Ex;
+    a.cnt = h->cnt;
+    const bool col = cmp == KNND_CMP_KL_REVERSE || cmp == KNND_CMP_SQEUCLIDEAN;
+    switch (h->MP) {
+    case 8: return col ? run_tma<8, true>(h, a) : run_tma<8, false>(h, a);
+    case 16: return col ? run_tma<16, true>(h, a) : run_tma<16, false>(h, a);
+    case 24: return col ? run_tma<24, true>(h, a) : run_tma<24, false>(h, a);
+    case 32: return col ? run_tma<32, true>(h, a) : run_tma<32, false>(h, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace knnd

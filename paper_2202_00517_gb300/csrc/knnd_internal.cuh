@@ -184,6 +184,7 @@ struct knnd_handle {
     int device;
     int num_sms;
     int fail_alloc_at;  // > 0: the fail_alloc_at-th workspace allocation fails (KNND_TEST_FAIL_ALLOC)
+    int join_lsu;       // 1: the mixed join gathers with plain loads even where the TMA form applies (KNND_JOIN=lsu)
     int allocs;
     bool prepared;
 
@@ -288,6 +289,11 @@ cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_
                         int split_den = 1);
 cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase,
                            int split_den);
+// The FP32 join with TMA-gathered rows and columns (join_tma.cu): the default
+// mixed-form join where tma_join_supported(h) holds.
+bool tma_join_supported(const knnd_handle *h);
+cudaError_t launch_join_tma(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase,
+                            int split_den);
 double bound_c_bf16x3(int MP);
 bool tc_supported(int MP, int K);
 cudaError_t launch_merge(knnd_handle *h, int32_t *idx, double *key, uint8_t *newflag);
