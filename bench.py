@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 from paper_2202_00517_gb300.datagen import dirichlet_points  # noqa: E402
 
 METRIC = "KNN-descent build s & KL evals/s, n=1e6 d=20 K=20: mixed vs FP64, % roofline"
+BATCH_METRIC = "KNN-descent batched build: KL evals/s over 4096 independent instances (n 200..50000, d 5/10/20, K 8/16/32)"
 UNIT = "KL evals/s"
 # name -> (n, m, K, seed, description)
 WORKLOADS = {
@@ -122,21 +123,69 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def join_traffic_per_launch(name):
+def join_traffic_per_launch(name, source="join.cu", profile_prefix="join_mixed"):
     """DRAM bytes per join launch from the committed ncu summary of the workload,
     if it was taken on the current join source (sha256 recorded in the summary);
     else None."""
-    src = os.path.join(ROOT, "paper_2202_00517_gb300", "csrc", "join.cu")
-    prof = os.path.join(ROOT, "profiles", f"join_mixed_{name}.md")
+    src = os.path.join(ROOT, "paper_2202_00517_gb300", "csrc", source)
+    prof = os.path.join(ROOT, "profiles", f"{profile_prefix}_{name}.md")
     if not os.path.exists(prof):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     text = open(prof).read()
-    m_sha = re.search(r"join\.cu sha256:\s*([0-9a-f]{64})", text)
+    m_sha = re.search(re.escape(source) + r" sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", text)
     if not (m_sha and m_b) or m_sha.group(1) != sha:
         return None
     return float(m_b.group(1))
+
+
+def tma_join_applies(m, k, comparator="kl"):
+    """The library's dispatch rule for the TMA-gathered FP32 join (mixed form,
+    up to 32 padded coordinates, K <= 32, no incremental proposals, not the inner
+    product): which kernel the roofline describes."""
+    return pad_m(m) <= 32 and k <= 32 and comparator != "inner" and os.environ.get("KNND_JOIN") != "lsu"
+
+
+FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz
+
+
+def fma_peaks(local, seconds=0.25):
+    """FMA pipe rates of this GPU, measured now with knnd_fma_peak (FP32 fma,
+    packed FP32 fma, FP64 fma; all SMs, 8 blocks of 256 threads each, eight
+    independent chains per thread), with the SM clocks sampled meanwhile.  Each
+    rate is the best of three launches of about `seconds`, and is also given at
+    the maximum SM clock (scaled by max / sampled median MHz)."""
+    import ctypes
+
+    import torch
+
+    from paper_2202_00517_gb300 import _lib
+    lib = _lib.load()
+    dev = torch.device("cuda", local)
+    sink = torch.zeros(4, dtype=torch.float32, device=dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    flops, ms = ctypes.c_double(), ctypes.c_float()
+    out = {}
+    clocks = Clocks(local)
+    clocks.start()
+    for kind, nm in ((0, "fp32_fma"), (1, "fp32x2_fma"), (2, "fp64_fma")):
+        _lib.check(lib.knnd_fma_peak(kind, 8, 1000, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(flops),
+                                     ctypes.byref(ms), stream), "knnd_fma_peak")
+        rate = flops.value / max(ms.value, 1e-3) * 1e3
+        iters = int(max(1000, min(2e8, 1000 * seconds * 1e3 / max(ms.value, 1e-3))))
+        best = 0.0
+        for _ in range(3):
+            _lib.check(lib.knnd_fma_peak(kind, 8, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(flops),
+                                         ctypes.byref(ms), stream), "knnd_fma_peak")
+            best = max(best, flops.value / (ms.value / 1e3) / 1e12)
+        out[nm] = best
+    clk = clocks.stop()
+    med, mx = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    scale = (mx / med) if (med and mx) else 1.0
+    return {"tflops": out, "tflops_at_max_clock": {k: v * scale for k, v in out.items()}, "clocks": clk,
+            "how": "knnd_fma_peak: 152 SMs x 8 blocks x 256 threads, 8 independent fma chains per thread, "
+                   "best of 3 CUDA-event-timed launches of ~0.25 s each; nothing set on the GPU"}
 
 
 # ---------------------------------------------------------------------------- reference arm
@@ -301,6 +350,7 @@ def gpu_single(args, name, rank, world, local, barrier):
         h.close()
         return {"ms": ms_total, "evals": ev_total, "infos": infos, "stats": st, "clocks": clk}
 
+    fma = fma_peaks(local) if not args.no_peaks else None
     clocks = Clocks(local)
     mixed = run_form(args.form, args.steps, args.warmup, clocks)
     fp64 = run_form("fp64", args.fp64_steps, 1) if args.fp64_steps > 0 else None
@@ -342,26 +392,46 @@ def gpu_single(args, name, rank, world, local, barrier):
     st = mixed["stats"]
     steps = args.steps
     value = world * mixed["evals"] / (mixed_ms / 1e3)
-    # dominant kernel: the join of the mixed form.  It gathers a random row of
-    # FP32 coordinates or logs per row and column of every hub tile, so HBM
-    # gather traffic bounds it.  Algorithmic bytes per launch: per hub
-    # (K + indeg) rows x (4 MP + 16) + K columns x (4 MP + 4) + (4 MP + 16), summed
-    # over hubs (sum of indeg = nK), plus 8 B per survivor written.  Every round
-    # takes every hub once; the first round's hubs run in two launches (split
-    # round), so the per-launch figures average over all the timed launches.
+    # dominant kernel: the join of the mixed form.  Its binding unit is the FP32
+    # fma pipe of the filter (the method's own work, 2 m FLOP per scored pair,
+    # n K (2K + 1) pairs per round); the HBM view counts the launch's compulsory
+    # bytes.  The first round's hubs run in two launches (split round), so the
+    # per-launch figures average over all the timed launches.
     join_ms = st["phase_ms"]["join"]
     join_n = max(1, st["phase_count"]["join"])
     join_avg_s = join_ms / join_n / 1e3
     MP = pad_m(M)
-    gather = N * ((2 * K + 1) * (4 * MP + 16) + K * (4 * MP + 4))
     rounds_t = sum(o["rounds"] for o in mixed["infos"])
-    bytes_per_launch = (rounds_t * gather + 8.0 * sum(o["join_survivors"] for o in mixed["infos"])) / join_n
+    surv_t = sum(o["join_survivors"] for o in mixed["infos"])
     flops_per_launch = 2.0 * M * N * K * (2 * K + 1) * rounds_t / join_n
+    # compulsory DRAM bytes of one launch: both FP32 tables (rows' coordinates and
+    # columns' logs), the friend and co-friend id lists, the co-friend offsets, the
+    # 16-byte row records, and the 8-byte entries of the survivors written
+    compulsory = 2.0 * N * MP * 4 + 2.0 * N * K * 4 + 8.0 * (N + 1) + 16.0 * N + 8.0 * surv_t / join_n
+    tma = args.form == "mixed" and tma_join_applies(M, K)
+    if tma:
+        kname, traffic = f"join_tma_kernel<{MP}, 0, 0>", join_traffic_per_launch(name, "join_tma.cu", "join_tma")
+    elif args.form == "mixed":
+        kname, traffic = f"join_mixed_kernel<{MP}, 0, 0, 0>", join_traffic_per_launch(name)
+    else:
+        kname, traffic = f"join_tc_kernel<{MP}>", None
     peaks, peak_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fp32_peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
-    achieved = bytes_per_launch / join_avg_s / 1e9
-    traffic = join_traffic_per_launch(name)
+    achieved_tf = flops_per_launch / join_avg_s / 1e12
+    fp32_meas = (fma["tflops_at_max_clock"]["fp32x2_fma" if tma else "fp32_fma"] if fma else None)
+    roofline = {
+        "kernel": kname, "bound": "alu", "achieved": achieved_tf, "peak": FP32_DERIVED_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved_tf / FP32_DERIVED_TFLOPS, "traffic": traffic,
+        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (the FP32 fma pipe of the filter)",
+        "peak_measured_tflops": fp32_meas,
+        "frac_of_measured": achieved_tf / fp32_meas if fp32_meas else None,
+        "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": join_avg_s * 1e3,
+        "launches_timed": join_n,
+        "hbm_view": {"compulsory_bytes_per_launch": compulsory, "achieved_gbs": compulsory / join_avg_s / 1e9,
+                     "peak_gbs": hbm_peak, "frac": compulsory / join_avg_s / 1e9 / hbm_peak,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6800 GB/s",
+                     "traffic_over_compulsory": traffic / compulsory if traffic else None}}
     total_ph = max(1e-9, sum(st["phase_ms"].values()))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -380,18 +450,8 @@ def gpu_single(args, name, rank, world, local, barrier):
         "join_survivors_per_build": info["join_survivors"],
         "phase_ms_per_build": {p: st["phase_ms"][p] / steps for p in st["phase_ms"]},
         "phase_share": {p: st["phase_ms"][p] / total_ph for p in st["phase_ms"]},
-        "roofline": {"kernel": f"join_mixed_kernel<{MP}, 0, 0, 0>" if args.form == "mixed" else f"join_tc_kernel<{MP}>",
-                     "bound": "hbm", "achieved": achieved,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                     else "fallback 6800 GB/s",
-                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": join_avg_s * 1e3,
-                     "launches_timed": join_n,
-                     "fp32_view": {"flops_per_launch": flops_per_launch,
-                                   "achieved_tflops": flops_per_launch / join_avg_s / 1e12,
-                                   "peak_tflops": fp32_peak,
-                                   "frac": flops_per_launch / join_avg_s / 1e12 / fp32_peak,
-                                   "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"}},
+        "roofline": roofline,
+        "fma_peaks": fma,
         "e2e": {"value": world * e2e_ev / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": N * M * 4, "d2h_bytes_per_step": N * K * (4 + 8)},
         "gpu_launches": st["kernel_launches"],
@@ -434,6 +494,15 @@ def gpu_single(args, name, rank, world, local, barrier):
         line["evals_per_s_fp64"] = world * fp64["evals"] / (fp64_ms / 1e3)
         line["speedup_mixed_vs_fp64"] = line["build_s_fp64"] / line["build_s_mixed"]
         line["fp64_join_ms_per_launch"] = fp64["stats"]["phase_ms"]["join"] / max(1, fp64["stats"]["phase_count"]["join"])
+        # the FP64 form's join against the FP64 fma pipe: 2 m FLOP per pair, as above
+        f64_n = max(1, fp64["stats"]["phase_count"]["join"])
+        f64_rounds = sum(o["rounds"] for o in fp64["infos"])
+        f64_flops = 2.0 * M * N * K * (2 * K + 1) * f64_rounds / f64_n
+        f64_ach = f64_flops / (line["fp64_join_ms_per_launch"] / 1e3) / 1e12
+        f64_peak = fma["tflops_at_max_clock"]["fp64_fma"] if fma else None
+        line["fp64_roofline"] = {"kernel": f"join_fp64_kernel<{MP}, 1>", "bound": "alu", "achieved": f64_ach,
+                                 "peak": f64_peak, "unit": "TFLOP/s", "frac": f64_ach / f64_peak if f64_peak else None,
+                                 "peak_source": "measured now (knnd_fma_peak, FP64 fma, at the maximum SM clock)"}
     if not args.no_cpu_baseline and name == "n1e6_d20_K20" and world == 1:  # rank 0 at N = 1 only
         import oracle
         pts64 = pts_host.numpy().astype(np.float64)
@@ -448,6 +517,52 @@ def gpu_single(args, name, rank, world, local, barrier):
     return line
 
 
+def gpu_leg(args, name, local, steps=2, warmup=1):
+    """A summary leg of the default run: the mixed-form build of another workload
+    (per-phase timing on, host round loop), and its BF16x3 tensor-core form once,
+    checked for the same graph."""
+    import torch
+
+    import paper_2202_00517_gb300 as knnd
+    n, m, k, seed, desc = WORKLOADS[name]
+    dev = torch.device("cuda", local)
+    pts = torch.from_numpy(dirichlet_points(n, m, seed, np.float32, threads=16)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": desc}
+    res = {}
+    for prec, st_, wu in (("mixed", steps, warmup), ("bf16x3", 1, 1)):
+        h = knnd.Handle(n, m, k, dtype="f32", precision=prec, timing=True, loop="host")
+        idx, key, flag = h.new_graph(dev)
+        for _ in range(wu):
+            h.build(pts, seed, idx, key, flag)
+        h.reset_stats()
+        torch.cuda.synchronize()
+        ms, ev = 0.0, 0
+        for _ in range(st_):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = h.build(pts, seed, idx, key, flag)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            ev += evals_of(n, k, r["rounds"])
+        st = h.stats()
+        h.close()
+        res[prec] = (r, idx, key)
+        out[prec] = {"build_s": ms / st_ / 1e3, "evals_per_s": ev / (ms / 1e3), "rounds": r["rounds"],
+                     "rescored_per_build": r["rescored"],
+                     "join_ms_per_launch": st["phase_ms"]["join"] / max(1, st["phase_count"]["join"]),
+                     "merge_ms_per_launch": st["phase_ms"]["merge"] / max(1, st["phase_count"]["merge"]),
+                     "join_kernel": (f"join_tma_kernel<{pad_m(m)}, 0, 0>" if prec == "mixed" and tma_join_applies(m, k)
+                                     else (f"join_mixed_kernel<{pad_m(m)}, 0, 0, 0>" if prec == "mixed"
+                                           else f"join_tc_kernel<{pad_m(m)}>"))}
+    a, b = res["mixed"], res["bf16x3"]
+    out["same_graph_bf16x3_vs_mixed"] = bool(a[0]["rounds"] == b[0]["rounds"] and torch.equal(a[1], b[1])
+                                            and torch.equal(a[2], b[2]))
+    return out
+
+
 def gpu_batch(args, rank, world, local, barrier):
     """The 4096-instance mix: batched form vs separate builds (a sample, scaled)."""
     import ctypes
@@ -458,7 +573,7 @@ def gpu_batch(args, rank, world, local, barrier):
     from paper_2202_00517_gb300 import _lib
     from paper_2202_00517_gb300.datagen import instance_mix
 
-    count, per_inst = 4096, args.batch_sample
+    count = 4096
     mix = instance_mix(count, 5)
     dev = torch.device("cuda", local)
     import concurrent.futures as cf
@@ -507,41 +622,79 @@ def gpu_batch(args, rank, world, local, barrier):
     lib.knnd_batch_info(b, ctypes.byref(nsub), ctypes.byref(ws), ctypes.byref(l1))
     lib.knnd_batch_destroy(b)
     evals = sum(evals_of(n, k, infos[i].rounds) for i, (n, m, k) in enumerate(mix))
-    # separate builds on an evenly spaced sample, bit-identity checked, time scaled to all instances
-    sel = np.linspace(0, count - 1, per_inst).astype(int)
-    sep, same = 0.0, 0
-    for i in sel:
-        n, m = pts[i].shape
-        h = knnd.Handle(n, m, Ks[i], dtype="f32", precision="mixed")
-        h.build(pts[i], seeds[i])
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        r = h.build(pts[i], seeds[i])
-        torch.cuda.synchronize()
-        sep += time.perf_counter() - t1
-        same += int(torch.equal(r["idx"], outs[i][0]) and torch.equal(r["key"], outs[i][1])
-                    and r["rounds"] == infos[i].rounds)
-        h.close()
-    sep_est = sep / len(sel) * count
+    # separate builds of every `stride`-th instance, issued from 16 host threads on
+    # 16 streams (one handle per instance, made before the timed region), checked
+    # bit for bit against the batched results; time scaled to all instances
+    sep = separate_builds_concurrent(pts, Ks, seeds, outs, [infos[i].rounds for i in range(count)],
+                                     stride=args.batch_stride, dev=dev)
     if rank != 0:
         return None
     return {
-        "metric": METRIC, "value": world * evals / batched_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": batched_s * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
+        "metric": BATCH_METRIC, "value": world * evals / batched_s, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
         "config": {"workload": "batched form: 4096 independent instances, n log-uniform in [200, 50000], "
                                "d in {5, 10, 20}, K in {8, 16, 32}, Dirichlet(1), seeds 0x5EED0000+i",
                    "points": int(sum(n for n, _, _ in mix)), "sub_batches": nsub.value,
                    "workspace_gb": ws.value / 1e9, "l2": "inputs larger than L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "batched_s": batched_s, "separate_builds_s_est": sep_est,
-        "separate_sample": f"{len(sel)} evenly spaced instances, each timed on its own warm handle, scaled to 4096",
-        "speedup_batched_vs_separate": sep_est / batched_s,
-        "identical_instances": f"{same}/{len(sel)}",
+        "batched_s": batched_s, "separate_builds_s_est": sep["est_s"],
+        "separate_sample": sep["how"], "speedup_batched_vs_separate": sep["est_s"] / batched_s,
+        "identical_instances": sep["identical"],
         "rounds_mean": float(np.mean([infos[i].rounds for i in range(count)])),
+        "merge_fallback_rows": int(sum(infos[i].merge_fallbacks for i in range(count))),
+        "rescored": int(sum(infos[i].rescored for i in range(count))),
         "gpu_launches": (l1.value - l0.value) // max(1, args.steps),
         "clocks": clk,
     }
+
+
+def separate_builds_concurrent(pts, Ks, seeds, outs, rounds, stride=4, dev=None, streams=16, wave=512):
+    """The per-instance baseline of the batched form: every `stride`-th instance
+    built by its own knnd_build (default graph round loop), the builds spread over
+    `streams` CUDA streams driven by as many host threads.  Handles are made per
+    wave of `wave` instances outside the timed region; the wall clock of each wave
+    (all its builds issued until all finished) is summed and scaled to all
+    instances."""
+    import concurrent.futures as cf
+
+    import torch
+
+    import paper_2202_00517_gb300 as knnd
+    sel = list(range(0, len(pts), stride))
+    strs = [torch.cuda.Stream(dev) for _ in range(streams)]
+    total, same = 0.0, 0
+    for w0 in range(0, len(sel), wave):
+        part = sel[w0:w0 + wave]
+        hs = []
+        for j, i in enumerate(part):
+            n, m = pts[i].shape
+            h = knnd.Handle(n, m, Ks[i], dtype="f32", precision="mixed", stream=strs[j % streams])
+            idx, key, flag = h.new_graph(dev)
+            hs.append((i, h, idx, key, flag))
+        for i, h, idx, key, flag in hs:  # warm: graph capture and first-use costs outside the timing
+            h.build(pts[i], seeds[i], idx, key, flag)
+        torch.cuda.synchronize()
+
+        def drive(lane):
+            res = []
+            for i, h, idx, key, flag in hs[lane::streams]:
+                res.append((i, h.build(pts[i], seeds[i], idx, key, flag)["rounds"]))
+            return res
+
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(streams) as ex:
+            done = [r for rr in ex.map(drive, range(streams)) for r in rr]
+        torch.cuda.synchronize()
+        total += time.perf_counter() - t0
+        rmap = dict(done)
+        for i, h, idx, key, flag in hs:
+            same += int(rmap[i] == rounds[i] and torch.equal(idx, outs[i][0]) and torch.equal(key, outs[i][1]))
+            h.close()
+    return {"est_s": total * len(pts) / len(sel), "identical": f"{same}/{len(sel)}",
+            "how": (f"{len(sel)} instances (every {stride}th), each its own knnd_build on one of {streams} "
+                    f"streams driven by {streams} host threads, handles made outside the timing; wall clock "
+                    f"scaled to {len(pts)}")}
 
 
 def pad_m(m):
@@ -564,8 +717,12 @@ def main():
                     help="skip the option legs (other join form, comparators, delta stop)")
     ap.add_argument("--form", default="mixed", choices=["mixed", "bf16x3"],
                     help="headline mixed form: FP32 CUDA-core join or BF16x3 tcgen05 join")
-    ap.add_argument("--batch-sample", type=int, default=256)
+    ap.add_argument("--batch-stride", type=int, default=4,
+                    help="separate-build baseline of the batched mix: every stride-th instance")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the n=4e6 d=64 K=32 and 4096-instance summary legs of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA pipe measurement")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -589,6 +746,19 @@ def main():
         line = gpu_batch(args, rank, world, local, barrier)
     else:
         line = gpu_single(args, args.workload, rank, world, local, barrier)
+        # the default run also records the other two benchmark workloads (one GPU only)
+        if world == 1 and args.workload == "n1e6_d20_K20" and not args.no_legs and args.steps > 0:
+            import torch
+            torch.cuda.empty_cache()
+            line["legs"] = {"n4e6_d64_K32": gpu_leg(args, "n4e6_d64_K32", local)}
+            torch.cuda.empty_cache()
+            bargs = argparse.Namespace(**vars(args))
+            bargs.steps, bargs.warmup = 2, 1
+            b = gpu_batch(bargs, rank, world, local, barrier)
+            line["legs"]["batch4096"] = {k: b[k] for k in (
+                "metric", "value", "unit", "ms_per_step", "batched_s", "separate_builds_s_est", "separate_sample",
+                "speedup_batched_vs_separate", "identical_instances", "rounds_mean", "gpu_launches", "config")}
+            torch.cuda.empty_cache()
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     barrier()

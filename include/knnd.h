@@ -280,6 +280,19 @@ knnd_status knnd_fcc_noalloc(const int32_t *idx, int64_t n, int32_t K, uint64_t 
  * Errors: EINVAL (null pointer with count > 0, count < 0 or >= 2^31), ECUDA. */
 knnd_status knnd_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int64_t count, void *stream);
 
+/* Measurement support for the roofline fractions the benchmark reports (not
+ * part of the method): the rate of one FMA pipe on the current device.  Runs
+ * blocks_per_sm blocks of 256 threads on every SM, each thread eight
+ * independent fma chains of `iters` steps: kind 0 FP32 fma (the join's filter
+ * arithmetic), 1 packed two-wide FP32 fma (FFMA2, the TMA join's form), 2 FP64
+ * fma (the FP64 form and the re-scores).  sink: device, >= 3 floats, all 0 on
+ * entry (operands the compiler cannot fold).  Returns the FLOPs executed
+ * (2 per fma, 4 per packed fma) in *flops and the CUDA-event milliseconds of the
+ * launch in *ms; synchronises `stream`.  Changes no device setting.
+ * Errors: EINVAL (kind, blocks_per_sm outside 1..64, iters < 1, null pointer), ECUDA. */
+knnd_status knnd_fma_peak(int32_t kind, int32_t blocks_per_sm, int64_t iters, float *sink, double *flops,
+                          float *ms, void *stream);
+
 /* Synchronise the handle's stream and return (and clear) the sticky device
  * status: EDOMAIN (bad coordinate), EINVAL (a graph index outside [0, n)
  * met by a kernel, which skipped it), EOVERFLOW (debug bucket check), or OK.

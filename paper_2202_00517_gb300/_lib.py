@@ -46,6 +46,7 @@ EXPORTS = [
     "knnd_fcc", "knnd_sync", "knnd_build", "knnd_build_host", "knnd_get_stats", "knnd_reset_stats",
     "knnd_status_string", "knnd_version", "knnd_fcc_noalloc", "knnd_batch_create", "knnd_batch_run",
     "knnd_batch_info", "knnd_batch_destroy", "knnd_build_batched", "knnd_philox4x32_10",
+    "knnd_fma_peak",
 ]
 
 KNND_NOALLOC_MAX_SAMPLES = 1 << 20
@@ -125,6 +126,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "knnd_batch_destroy": (None, [P]),
         "knnd_build_batched": (i32, [i32, P, i32, i32, ctypes.POINTER(knnd_params), i64, P, P]),
         "knnd_philox4x32_10": (i32, [P, P, i64, P]),
+        "knnd_fma_peak": (i32, [i32, i32, i64, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -225,8 +225,9 @@ struct knnd_handle {
     // u = key rounded up to FP32.  FP64 form: the exact key at the same slot.
     int2 *bent;
     double *bkey;
-    int32_t *fb_list;   // n: rows the merge's fast path leaves to the serial path
+    int32_t *fb_list;   // n: rows the merge's fast path leaves to its second kernel
     int32_t *fb_count;
+    double *fb_T;       // n: the bound T of each such row's K-th key
     // counters
     int64_t *cnt;       // kCntNum device counters
     int64_t *cnt_host;  // pinned mirror

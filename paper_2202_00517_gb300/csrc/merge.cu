@@ -19,9 +19,12 @@
 //     or (when more than 32 candidates pass) the bound of the K-th smallest
 //     distinct (u, index) kept, by K rounds of warp argmin;
 //  3. if some lane pushed out an entry that could still reach T, the row is
-//     listed and finished by a second kernel on the serial path; otherwise the kept entries that can reach
-//     T get their exact key (FP64 form: stored; mixed form: canonical FP64
-//     re-score) and are inserted into the old list one by one.
+//     listed (with T) for a second kernel, which streams its bucket again 32
+//     entries at a time and keys and inserts, by the batched insertion, every
+//     entry whose lower bound reaches min(T, the list's current K-th key)
+//     (K > 32: one at a time, on the serial path); otherwise the kept entries
+//     that can reach T get their exact key (FP64 form: stored; mixed form:
+//     canonical FP64 re-score) and are inserted into the old list.
 // The result equals the FP64 form's bit for bit.
 #include <math_constants.h>
 
@@ -151,8 +154,9 @@ struct MergeArgs {
     const double *Ex;
     int64_t *cnt;
     int32_t *err;
-    int32_t *fb_list;   // rows left to the serial path
+    int32_t *fb_list;   // rows left to the second kernel
     int32_t *fb_count;
+    double *fb_T;       // per row: the upper bound T of its K-th key the fast path found (K <= 32)
     InstView iv;
 };
 
@@ -537,6 +541,66 @@ __device__ __forceinline__ void insert_batch(WarpList<1> &X, int K, int lane, ui
     X.kth(K, xk, xi);
 }
 
+// Rows of K <= 32 whose kept entries do not cover every entry that can reach
+// T.  The bucket is scanned 32 entries at a time; the entries whose lower
+// bound reaches min(T, the list's K-th key) are compacted into `pend` (kPend
+// per warp, by ballot), and each time it holds at least 32 (and at the end)
+// they are keyed and inserted 32 at a time by the batched insertion, skipping
+// those that the list has left behind meanwhile.  (The pending list is drained
+// whenever the next 32 entries might not fit, and at the end.)
+constexpr int kPend = 256;
+
+template <bool MIXED, int CMP>
+__device__ __forceinline__ void stream_row(const MergeArgs &a, int64_t x, int lane, WarpList<1> &X, const int *tab,
+                                        int64_t base, int cnt, const Bounds<MIXED> &B, double T, long long &rescored,
+                                        BatchScratch &sb, int2 *pend)
+{
+    const int K = a.K;
+    const unsigned lt = lanemask_lt();
+    uint64_t xk;
+    int xi;
+    X.kth(K, xk, xi);
+    int np = 0;  // entries pending in pend: (index, bucket slot)
+    auto drain = [&]() {
+        for (int c0 = 0; c0 < np; c0 += 32) {
+            const bool has = c0 + lane < np;
+            int ci = -1;
+            uint64_t k = ~0ull;
+            bool want = false;
+            if (has) {
+                const int2 e = pend[c0 + lane];
+                ci = e.x;
+                const uint32_t u = (uint32_t)a.bent[base + e.y].x;
+                want = u <= sortable_bits(B.u_reach(fmin(T, from_dkey(xk))));
+                if (want) {
+                    if (MIXED) {
+                        k = dkey(rescore_dir<CMP, true>(a, x, ci, B.nh));
+                        rescored += 1;
+                    } else {
+                        k = dkey(a.bkey[base + e.y]);
+                    }
+                }
+            }
+            insert_batch(X, K, lane, k, ci, want, xk, xi, sb);
+        }
+        np = 0;
+        __syncwarp();
+    };
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const bool has = c0 + lane < cnt;
+        const int2 en = has ? a.bent[base + c0 + lane] : make_int2(0, -1);
+        const int ci = en.y;
+        const uint32_t lim = sortable_bits(B.u_reach(fmin(T, from_dkey(xk))));
+        const bool want = has && ci >= 0 && ci < a.n && (uint32_t)en.x <= lim && !hash_has(tab, ci);
+        const unsigned m = __ballot_sync(0xffffffffu, want);
+        if (np + __popc(m) > kPend) drain();
+        if (want) pend[np + __popc(m & lt)] = make_int2(ci, c0 + lane);
+        np += __popc(m);
+        __syncwarp();
+    }
+    drain();
+}
+
 template <int NE, int R, bool MIXED, int CMP>
 __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &X, const int *tab, int2 *live_list,
                          int64_t base, int cnt, const Bounds<MIXED> &B, long long &rescored, BatchScratch &sb)
@@ -585,7 +649,10 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
         if (count == K) T = fmin(T, B.upper(from_sortable_bits(mu)));
     }
     const uint32_t reach = sortable_bits(B.u_reach(T));
-    if (__any_sync(0xffffffffu, L.drop <= reach)) return false;
+    if (__any_sync(0xffffffffu, L.drop <= reach)) {
+        if (lane == 0) a.fb_T[x] = T;  // the second kernel streams the bucket against it
+        return false;
+    }
     // compact the entries that can reach T, then key them 32 at a time
     const unsigned lt = lanemask_lt();
     int nlive = 0;
@@ -660,8 +727,10 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
             if (!fast_row<NE, R, MIXED, CMP>(a, x, lane, X, tab, live_list, base, cnt, B, rescored,
                                         s_batch[NE == 1 ? (threadIdx.x >> 5) : 0])) {
                 // the row stays as it is here; merge_fallback_kernel finishes it
-                if (lane == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)x;
-                fallbacks += 1;
+                if (lane == 0) {
+                    a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)x;
+                    fallbacks += 1;  // once per row (the counts are summed over the lanes)
+                }
                 flush_row_counts(a, x, newcount, rescored, fallbacks);
                 continue;
             }
@@ -674,9 +743,11 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
 
 // Rows the fast path could not settle, one warp each, on the serial path.
 template <int NE, bool MIXED, int CMP>
-__global__ void __launch_bounds__(256) merge_fallback_kernel(MergeArgs a)
+__global__ void __launch_bounds__(256, 2) merge_fallback_kernel(MergeArgs a)
 {
     __shared__ int s_hash[8][kHashSlots];
+    __shared__ BatchScratch s_batch[NE == 1 ? 8 : 1];
+    __shared__ int2 s_pend[NE == 1 ? 8 : 1][NE == 1 ? kPend : 1];
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int K = a.K;
@@ -694,7 +765,11 @@ __global__ void __launch_bounds__(256) merge_fallback_kernel(MergeArgs a)
         B.nh = (MIXED && CMP != KNND_CMP_KL_REVERSE) ? a.negH[x] : 0.0;
         B.E = MIXED ? a.Ex[x] : 0.0;
         hash_fill(tab, lane, K, X);
-        serial_row<NE, MIXED, CMP>(a, x, lane, X, tab, base, cnt, B, rescored);
+        if constexpr (NE == 1)  // the threshold T the fast path found for the row
+            stream_row<MIXED, CMP>(a, x, lane, X, tab, base, cnt, B, a.fb_T[x], rescored, s_batch[threadIdx.x >> 5],
+                                   s_pend[threadIdx.x >> 5]);
+        else
+            serial_row<NE, MIXED, CMP>(a, x, lane, X, tab, base, cnt, B, rescored);
         write_row(a, x, lane, X, newcount);
         long long nofb = 0;
         flush_row_counts(a, x, newcount, rescored, nofb);
@@ -744,6 +819,7 @@ cudaError_t launch_merge_from(knnd_handle *h, const int32_t *in_idx, const doubl
     const int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * 8);
     a.fb_list = h->fb_list;
     a.fb_count = h->fb_count;
+    a.fb_T = h->fb_T;
     a.iv = h->iv;
     cudaMemsetAsync(h->fb_count, 0, sizeof(int32_t), h->stream);
     const bool fp64 = h->prec == KNND_PREC_FP64;
