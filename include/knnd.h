@@ -304,8 +304,12 @@ knnd_status knnd_sync(knnd_handle *h);
  * Many independent instances built together (the same method, per instance,
  * as knnd_build).  Instances with equal (m, K) share kernel launches: each
  * phase is one launch over all of them; a class too large for the workspace
- * budget is cut into sub-batches run one after the other.  Every instance gets
- * the graph, rounds and counts a separate knnd_build with its seed would give. */
+ * budget is cut into sub-batches.  Each sub-batch runs as one CUDA graph
+ * (captured at the first knnd_batch_run and kept): its rounds are a
+ * conditional while loop whose stop test runs on the device, per instance.
+ * Sub-batches run on up to four internal streams at once, each with its own
+ * workspace.  Every instance gets the graph, rounds and counts a separate
+ * knnd_build with its seed would give. */
 typedef struct {
     const void *points; /* device: n x m, row stride ld elements, dtype of the call */
     int64_t ld;
@@ -320,18 +324,22 @@ typedef struct {
 typedef struct knnd_batch knnd_batch;
 
 /* Plan the sub-batches of `count` instances (the array is copied; the points
- * and output pointers must stay valid until knnd_batch_run returns) and
- * allocate one workspace for the largest of them.  workspace_limit: device
- * bytes a sub-batch may plan for (<= 0: 32 GiB).  Errors: EINVAL (a bad
- * instance or parameter), ENOMEM, ECUDA. */
+ * and output pointers must stay valid until the batch is destroyed) and
+ * allocate the workspaces.  workspace_limit: device bytes one sub-batch may
+ * plan for (<= 0: 32 GiB); up to four workspaces, each the size of the largest
+ * sub-batch given to it, as many as 85 % of the free device memory holds.
+ * Errors: EINVAL (a bad instance or parameter), ENOMEM, ECUDA. */
 knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instance *inst, knnd_dtype dtype,
                               knnd_precision precision, const knnd_params *params, int64_t workspace_limit,
                               void *stream);
 
 /* Build every instance (Sec. 3: initial graph, rounds to the statistical
- * stop, per instance).  info: host array of `count` reports, or NULL.
- * Synchronises the stream once per round of each sub-batch.
- * Errors: EDOMAIN, EINVAL (bad index met on the device), ECUDA. */
+ * stop, per instance).  The work starts after what is already enqueued on the
+ * batch's stream, and the stream waits for it; the call returns when every
+ * instance is built (no synchronisation inside a sub-batch).  info: host
+ * array of `count` reports, or NULL.  A bad coordinate (EDOMAIN) or index
+ * (EINVAL) met on the device is reported once every sub-batch has run; the
+ * outputs are then unspecified.  Errors: EDOMAIN, EINVAL, ECUDA. */
 knnd_status knnd_batch_run(knnd_batch *b, knnd_build_info *info);
 
 /* Sub-batches planned, workspace bytes, kernels launched so far (each NULL-able). */

@@ -10,10 +10,23 @@
 // taken on the device; a stopped instance's hubs and rows are skipped.  Every
 // instance therefore gets exactly the graph, rounds and counts a separate
 // knnd_build would give it.
+//
+// Execution.  Each sub-batch is one CUDA graph, captured at the first run and
+// kept: the set-up, the initial graph, round 1 (split) and its stop test, then a
+// conditional while node whose body is one round, the clustering sample and the
+// per-instance stop test, whose last kernel keeps the loop going while any
+// instance of the sub-batch is active; then the export of every instance's
+// graph.  No host synchronisation happens inside a run.  Sub-batches are spread
+// over up to kMaxSlots workspaces ("slots"), each with its own stream, so that
+// up to kMaxSlots sub-batches run at once: the phases of one (the merge's FP64
+// re-scores, the small per-round kernels, the tail of its last rounds) overlap
+// the joins of another.  A slot runs its sub-batches in order; sub-batches go
+// to slots largest first, each to the slot with the least work so far.
 #include <algorithm>
 #include <cstring>
 #include <map>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "knnd_internal.cuh"
@@ -22,11 +35,7 @@ using namespace knnd;
 
 namespace {
 
-struct SubBatch {
-    int32_t m, K;
-    std::vector<int32_t> members;  // indices into the instance array
-    int64_t npts;
-};
+constexpr int kMaxSlots = 4;
 
 __global__ void fill_inst_of_kernel(const int64_t *__restrict__ base, int32_t ninst, int64_t n, int32_t *of)
 {
@@ -54,7 +63,8 @@ struct History {
     int64_t *fallback;  // ninst
     int32_t *rounds;    // ninst
     int32_t *reason;    // ninst
-    int32_t *nactive;   // 1
+    int32_t *nactive;   // 1: instances still active after the current round
+    int32_t *round;     // 1: the round the device-driven loop is in
 };
 
 __global__ void record_hits0_kernel(InstView iv, int32_t ninst, History hs, int32_t max_rounds)
@@ -64,12 +74,25 @@ __global__ void record_hits0_kernel(InstView iv, int32_t ninst, History hs, int3
     hs.hits[(int64_t)i * (max_rounds + 1)] = iv.cnt[(int64_t)i * kCntNum + kCntHits];
 }
 
+// Start of a round of the loop: round number + 1, the instances' counters and
+// the active count cleared.
+__global__ void round_begin_kernel(History hs, int64_t *cnt, int32_t ninst)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < (int64_t)ninst * kCntNum) cnt[t] = 0;
+    if (t == 0) {
+        *hs.round += 1;
+        *hs.nactive = 0;
+    }
+}
+
 // After round r: per-instance stop decision of Sec. 3.3 (iv) (hits of round r
 // not above those of round r-1), or no update, or the round cap.
-__global__ void stop_kernel(InstView iv, int32_t *active, int32_t ninst, History hs, int32_t r, int32_t max_rounds,
+__global__ void stop_kernel(InstView iv, int32_t *active, int32_t ninst, History hs, int32_t max_rounds,
                             int32_t stop_on_zero, float stop_delta, int32_t K)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t r = *hs.round;
     if (i >= ninst || !active[i]) return;
     const int64_t *c = iv.cnt + (int64_t)i * kCntNum;
     const int64_t upd = c[kCntUpdates], hits = c[kCntHits];
@@ -92,6 +115,12 @@ __global__ void stop_kernel(InstView iv, int32_t *active, int32_t ninst, History
     }
 }
 
+// Last kernel of a round: the loop goes on while an instance is active.
+__global__ void loop_cond_kernel(History hs, cudaGraphConditionalHandle cond)
+{
+    cudaGraphSetConditional(cond, *hs.nactive > 0 ? 1u : 0u);
+}
+
 // Global graph -> each instance's own arrays, indices made local.
 __global__ void export_kernel(const int32_t *__restrict__ idx, const double *__restrict__ key, int64_t n, int K,
                               InstView iv, int32_t *const *out_idx, double *const *out_key)
@@ -107,35 +136,51 @@ __global__ void export_kernel(const int32_t *__restrict__ idx, const double *__r
     out_key[i][o] = key[e];
 }
 
+// One sub-batch: its instances, their device tables (made once, at creation),
+// its history and its CUDA graph.
+struct SubBatch {
+    int32_t m, K;
+    std::vector<int32_t> members;  // indices into the instance array
+    int64_t npts;
+    double work;  // n K (2K + 1) summed: the pairs of one round
+    int slot;
+    int64_t *base;       // ninst + 1
+    int32_t *n;
+    uint64_t *seed;
+    const void **ptrs;
+    int64_t *lds;
+    int32_t **oidx;
+    double **okey;
+    History hs;
+    cudaGraphExec_t exec;
+    int64_t launches_outer;  // kernels outside the loop body (set-up, round 1, export)
+    int64_t launches_round;  // kernels of one round of the body
+};
+
+// A workspace and its stream: runs its sub-batches one after the other.
+struct Slot {
+    knnd_handle *h;  // sized for the largest of its sub-batches
+    cudaStream_t stream;
+    cudaEvent_t done;
+    int32_t *idx;    // working graph
+    double *key;
+    std::vector<int> subs;
+    double work;
+};
+
 }  // namespace
 
 struct knnd_batch {
     std::vector<knnd_instance> inst;
     std::vector<SubBatch> subs;
+    std::vector<Slot> slots;
     knnd_dtype dtype;
     knnd_precision prec;
     knnd_params prm;
-    cudaStream_t stream;
-    knnd_handle *h;   // workspace sized for the largest sub-batch
-    int32_t *idx;     // working graph
-    double *key;
-    const void **ptrs;  // device per-instance tables of the current sub-batch
-    int64_t *lds;
-    int32_t **oidx;
-    double **okey;
-    History hs;
-    int32_t ninst_cap;
-    // pinned host staging
-    int64_t *h_base;
-    int32_t *h_n;
-    uint64_t *h_seed;
-    const void **h_ptrs;
-    int64_t *h_lds;
-    int32_t **h_oidx;
-    double **h_okey;
-    int32_t *h_nactive;
-    int64_t *h_upd, *h_hits, *h_resc, *h_fb;
-    int32_t *h_rounds, *h_reason;
+    cudaStream_t stream;  // the caller's
+    cudaEvent_t start;
+    int64_t launches;
+    int64_t ws_bytes;
 };
 
 namespace {
@@ -153,30 +198,26 @@ knnd_status balloc(T **p, int64_t count)
     return KNND_OK;
 }
 
-template <typename T>
-knnd_status halloc(T **p, int64_t count)
+void free_sub(SubBatch &sb)
 {
-    *p = nullptr;
-    if (count <= 0) count = 1;
-    if (cudaMallocHost((void **)p, sizeof(T) * (size_t)count) != cudaSuccess) {
-        (void)cudaGetLastError();
-        *p = nullptr;
-        return KNND_ENOMEM;
-    }
-    return KNND_OK;
+    if (sb.exec) cudaGraphExecDestroy(sb.exec);
+    void *dev[] = {sb.base, sb.n, sb.seed, sb.ptrs, sb.lds, sb.oidx, sb.okey, sb.hs.upd, sb.hs.hits,
+                   sb.hs.rescored, sb.hs.fallback, sb.hs.rounds, sb.hs.reason, sb.hs.nactive, sb.hs.round};
+    for (void *p : dev)
+        if (p) cudaFree(p);
 }
 
 void batch_free(knnd_batch *b)
 {
-    if (b->h) destroy_handle(b->h);
-    void *dev[] = {b->idx, b->key, b->ptrs, b->lds, b->oidx, b->okey, b->hs.upd, b->hs.hits, b->hs.rescored,
-                   b->hs.fallback, b->hs.rounds, b->hs.reason, b->hs.nactive};
-    for (void *p : dev)
-        if (p) cudaFree(p);
-    void *hst[] = {b->h_base, b->h_n, b->h_seed, b->h_ptrs, b->h_lds, b->h_oidx, b->h_okey, b->h_nactive,
-                   b->h_upd, b->h_hits, b->h_resc, b->h_fb, b->h_rounds, b->h_reason};
-    for (void *p : hst)
-        if (p) cudaFreeHost(p);
+    for (SubBatch &sb : b->subs) free_sub(sb);
+    for (Slot &sl : b->slots) {
+        if (sl.h) destroy_handle(sl.h);
+        if (sl.idx) cudaFree(sl.idx);
+        if (sl.key) cudaFree(sl.key);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    if (b->start) cudaEventDestroy(b->start);
     delete b;
 }
 
@@ -186,112 +227,182 @@ int64_t bytes_per_point(int32_t m, int32_t K, bool mixed, bool incremental)
     const int64_t MP = pad_coords(m);
     const int64_t bucket = (int64_t)K * (2 * K + 1) * (mixed ? 8 : 16);
     // tables, per-row scalars, buckets, CSR and arc slots, graph, the split round's graph copy (13 B per arc)
-    return MP * 24 + 96 + bucket + (int64_t)K * (4 + 4 + 4 + 8 + 13 + (incremental ? 2 : 0));
+    return MP * 24 + 104 + bucket + (int64_t)K * (4 + 4 + 4 + 8 + 13 + (incremental ? 2 : 0));
 }
 
-// One sub-batch: all its instances from points to graphs.
-knnd_status run_sub(knnd_batch *b, const SubBatch &sb, knnd_build_info *info)
+// The sub-batch's device tables and history, filled once (synchronous copies).
+knnd_status make_sub_tables(knnd_batch *b, SubBatch &sb)
 {
-    knnd_handle *h = b->h;
-    cudaStream_t st = b->stream;
     const int32_t ni = (int32_t)sb.members.size();
     const int32_t R = b->prm.max_rounds;
-    configure(h, sb.npts, sb.m, sb.K);
-    h->ninst = ni;
+    knnd_status s = balloc(&sb.base, ni + 1);
+    if (!s) s = balloc(&sb.n, ni);
+    if (!s) s = balloc(&sb.seed, ni);
+    if (!s) s = balloc(&sb.ptrs, ni);
+    if (!s) s = balloc(&sb.lds, ni);
+    if (!s) s = balloc(&sb.oidx, ni);
+    if (!s) s = balloc(&sb.okey, ni);
+    if (!s) s = balloc(&sb.hs.upd, (int64_t)ni * R);
+    if (!s) s = balloc(&sb.hs.hits, (int64_t)ni * (R + 1));
+    if (!s) s = balloc(&sb.hs.rescored, ni);
+    if (!s) s = balloc(&sb.hs.fallback, ni);
+    if (!s) s = balloc(&sb.hs.rounds, ni);
+    if (!s) s = balloc(&sb.hs.reason, ni);
+    if (!s) s = balloc(&sb.hs.nactive, 1);
+    if (!s) s = balloc(&sb.hs.round, 1);
+    if (s) return s;
+    std::vector<int64_t> base(ni + 1), lds(ni);
+    std::vector<int32_t> n(ni);
+    std::vector<uint64_t> seed(ni);
+    std::vector<const void *> ptrs(ni);
+    std::vector<int32_t *> oidx(ni);
+    std::vector<double *> okey(ni);
     int64_t off = 0;
     for (int32_t j = 0; j < ni; ++j) {
         const knnd_instance &in = b->inst[sb.members[j]];
-        b->h_base[j] = off;
-        b->h_n[j] = (int32_t)in.n;
-        b->h_seed[j] = in.seed;
-        b->h_ptrs[j] = in.points;
-        b->h_lds[j] = in.ld;
-        b->h_oidx[j] = in.idx;
-        b->h_okey[j] = in.key;
+        base[j] = off;
+        n[j] = (int32_t)in.n;
+        seed[j] = in.seed;
+        ptrs[j] = in.points;
+        lds[j] = in.ld;
+        oidx[j] = in.idx;
+        okey[j] = in.key;
         off += in.n;
     }
-    b->h_base[ni] = off;
-    cudaError_t e = cudaMemcpyAsync(h->inst_base, b->h_base, sizeof(int64_t) * (ni + 1), cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(h->inst_n, b->h_n, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(h->inst_seed, b->h_seed, sizeof(uint64_t) * ni, cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(b->ptrs, b->h_ptrs, sizeof(void *) * ni, cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(b->lds, b->h_lds, sizeof(int64_t) * ni, cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(b->oidx, b->h_oidx, sizeof(int32_t *) * ni, cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(b->okey, b->h_okey, sizeof(double *) * ni, cudaMemcpyHostToDevice, st);
-    // every instance active, counters and history cleared
-    if (!e) {
-        set_ones_kernel<<<(ni + 255) / 256, 256, 0, st>>>(h->inst_active, ni);
-        e = cudaGetLastError();
-    }
-    if (!e) e = cudaMemsetAsync(b->hs.rescored, 0, sizeof(int64_t) * ni, st);
-    if (!e) e = cudaMemsetAsync(b->hs.fallback, 0, sizeof(int64_t) * ni, st);
-    if (!e) e = cudaMemsetAsync(b->hs.upd, 0, sizeof(int64_t) * ni * R, st);
-    if (!e) e = cudaMemsetAsync(b->hs.hits, 0, sizeof(int64_t) * ni * (R + 1), st);
-    if (e) return status_of(e);
+    base[ni] = off;
+    cudaError_t e = cudaMemcpy(sb.base, base.data(), sizeof(int64_t) * (ni + 1), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(sb.n, n.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(sb.seed, seed.data(), sizeof(uint64_t) * ni, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(sb.ptrs, ptrs.data(), sizeof(void *) * ni, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(sb.lds, lds.data(), sizeof(int64_t) * ni, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(sb.oidx, oidx.data(), sizeof(int32_t *) * ni, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(sb.okey, okey.data(), sizeof(double *) * ni, cudaMemcpyHostToDevice);
+    return status_of(e);
+}
+
+// Points the slot's handle at the sub-batch (its shape and instance tables).
+void bind_sub(Slot &sl, const SubBatch &sb)
+{
+    knnd_handle *h = sl.h;
+    configure(h, sb.npts, sb.m, sb.K);
+    h->ninst = (int32_t)sb.members.size();
     h->iv.of = h->inst_of;
-    h->iv.base = h->inst_base;
-    h->iv.n = h->inst_n;
-    h->iv.seed = h->inst_seed;
+    h->iv.base = sb.base;
+    h->iv.n = sb.n;
+    h->iv.seed = sb.seed;
     h->iv.active = h->inst_active;
     h->iv.cnt = h->inst_cnt;
+}
+
+// Captures the sub-batch's whole build into one CUDA graph (on its slot's
+// stream) and instantiates it:
+//   set-up, precompute, initial graphs, hits of G_0;
+//   round 1 (split), its sample and stop test, the loop condition;
+//   while (an instance is active) { round, sample, stop test, condition };
+//   export of each instance's graph.
+knnd_status capture_sub(knnd_batch *b, SubBatch &sb)
+{
+    Slot &sl = b->slots[sb.slot];
+    knnd_handle *h = sl.h;
+    cudaStream_t st = sl.stream;
+    bind_sub(sl, sb);
+    const int32_t ni = (int32_t)sb.members.size();
+    const int32_t R = b->prm.max_rounds;
     const int T = 256;
-    fill_inst_of_kernel<<<(unsigned)((sb.npts + T - 1) / T), T, 0, st>>>(h->inst_base, ni, sb.npts, h->inst_of);
-    h->launches += 1;
-    // precompute (EDOMAIN is reported here), initial graphs, clustering hits of G_0
-    e = launch_precompute_from(h, nullptr, 0, b->ptrs, b->lds);
-    if (e) return status_of(e);
-    knnd_status s = take_error(h);
-    if (s) return s;
+    const unsigned iblocks = (unsigned)((ni + T - 1) / T);
+    const unsigned cblocks = (unsigned)(((int64_t)ni * kCntNum + T - 1) / T);
     uint8_t *flag = b->prm.incremental ? h->flag_tmp : nullptr;  // incremental proposals
-    e = launch_init_graph(h, 0, b->idx, b->key, flag);
-    if (!e) e = cudaMemsetAsync(h->inst_cnt, 0, sizeof(int64_t) * ni * kCntNum, st);
-    if (!e) e = launch_fcc_batch(h, b->idx, 0);
+    const int64_t l0 = h->launches;
+    const int64_t r0 = h->rounds_run;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
     if (e) return status_of(e);
-    record_hits0_kernel<<<(ni + T - 1) / T, T, 0, st>>>(h->iv, ni, b->hs, R);
-    h->launches += 1;
-    for (int32_t r = 1; r <= R; ++r) {
-        e = cudaMemsetAsync(h->inst_cnt, 0, sizeof(int64_t) * ni * kCntNum, st);
-        if (!e) e = cudaMemsetAsync(b->hs.nactive, 0, sizeof(int32_t), st);
-        if (e) return status_of(e);
-        s = round_ops(h, 0, r, b->idx, b->key, flag, nullptr);
-        if (s) return s;
-        e = launch_fcc_batch(h, b->idx, r);
-        if (e) return status_of(e);
-        stop_kernel<<<(ni + T - 1) / T, T, 0, st>>>(h->iv, h->inst_active, ni, b->hs, r, R,
-                                                    b->prm.stop_on_zero_updates, b->prm.stop_delta, sb.K);
-        h->launches += 1;
-        e = cudaMemcpyAsync(b->h_nactive, b->hs.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaStreamSynchronize(st);
-        if (e) return status_of(e);
-        if (*b->h_nactive == 0) break;
-    }
-    const int64_t nK = sb.npts * sb.K;
-    export_kernel<<<(unsigned)((nK + T - 1) / T), T, 0, st>>>(b->idx, b->key, sb.npts, sb.K, h->iv, b->oidx, b->okey);
-    h->launches += 1;
-    s = take_error(h);
-    if (s) return s;
-    if (info) {
-        e = cudaMemcpyAsync(b->h_upd, b->hs.upd, sizeof(int64_t) * ni * R, cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaMemcpyAsync(b->h_hits, b->hs.hits, sizeof(int64_t) * ni * (R + 1), cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaMemcpyAsync(b->h_resc, b->hs.rescored, sizeof(int64_t) * ni, cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaMemcpyAsync(b->h_fb, b->hs.fallback, sizeof(int64_t) * ni, cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaMemcpyAsync(b->h_rounds, b->hs.rounds, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaMemcpyAsync(b->h_reason, b->hs.reason, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaStreamSynchronize(st);
-        if (e) return status_of(e);
-        for (int32_t j = 0; j < ni; ++j) {
-            const knnd_instance &in = b->inst[sb.members[j]];
-            knnd_build_info &o = info[sb.members[j]];
-            std::memset(&o, 0, sizeof(o));
-            o.rounds = b->h_rounds[j];
-            o.stop_reason = b->h_reason[j];
-            for (int32_t r = 0; r < o.rounds; ++r) o.updates[r] = b->h_upd[(int64_t)j * R + r];
-            for (int32_t r = 0; r <= o.rounds; ++r) o.fcc_hits[r] = b->h_hits[(int64_t)j * (R + 1) + r];
-            o.init_pairs = in.n * in.K;
-            o.proposals = (int64_t)o.rounds * in.n * in.K * (2 * (int64_t)in.K + 1);
-            o.rescored = b->h_resc[j];
-            o.merge_fallbacks = b->h_fb[j];
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, g, 0, 0);
+    knnd_status s = KNND_OK;
+    std::vector<cudaGraphNode_t> tail;
+    // one round of the loop: the round, the sample, the stop test, the condition
+    auto round_body = [&](int32_t round) {
+        round_begin_kernel<<<cblocks, T, 0, st>>>(sb.hs, h->inst_cnt, ni);
+        const knnd_status rs = round_ops(h, 0, round, sl.idx, sl.key, flag, nullptr);
+        if (rs && !s) s = rs;
+        launch_fcc_batch(h, sl.idx, 0, sb.hs.round);
+        stop_kernel<<<iblocks, T, 0, st>>>(h->iv, h->inst_active, ni, sb.hs, R, b->prm.stop_on_zero_updates,
+                                           b->prm.stop_delta, sb.K);
+        loop_cond_kernel<<<1, 1, 0, st>>>(sb.hs, cond);
+        h->launches += 3;
+    };
+    auto end_capture = [&](cudaGraph_t into_out, bool keep_tail) -> cudaError_t {
+        cudaError_t c = cudaGetLastError();
+        if (keep_tail && c == cudaSuccess) {
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t *d = nullptr;
+            size_t nd = 0;
+            c = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &d, nullptr, &nd);
+            if (c == cudaSuccess) tail.assign(d, d + nd);
         }
+        cudaGraph_t out = nullptr;
+        const cudaError_t c2 = cudaStreamEndCapture(st, &out);
+        (void)into_out;
+        return c != cudaSuccess ? c : c2;
+    };
+    // set-up through round 1
+    if (!e) e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (!e) {
+        set_ones_kernel<<<iblocks, T, 0, st>>>(h->inst_active, ni);
+        cudaMemsetAsync(sb.hs.rescored, 0, sizeof(int64_t) * ni, st);
+        cudaMemsetAsync(sb.hs.fallback, 0, sizeof(int64_t) * ni, st);
+        cudaMemsetAsync(sb.hs.upd, 0, sizeof(int64_t) * ni * R, st);
+        cudaMemsetAsync(sb.hs.hits, 0, sizeof(int64_t) * ni * (R + 1), st);
+        cudaMemsetAsync(sb.hs.round, 0, sizeof(int32_t), st);
+        fill_inst_of_kernel<<<(unsigned)((sb.npts + T - 1) / T), T, 0, st>>>(sb.base, ni, sb.npts, h->inst_of);
+        h->launches += 2;
+        cudaError_t c = launch_precompute_from(h, nullptr, 0, sb.ptrs, sb.lds);
+        if (!c) c = launch_init_graph(h, 0, sl.idx, sl.key, flag);
+        if (!c) c = cudaMemsetAsync(h->inst_cnt, 0, sizeof(int64_t) * ni * kCntNum, st);
+        if (!c) c = launch_fcc_batch(h, sl.idx, 0);
+        if (c && !s) s = status_of(c);
+        record_hits0_kernel<<<iblocks, T, 0, st>>>(h->iv, ni, sb.hs, R);
+        h->launches += 1;
+        round_body(1);
+        e = end_capture(g, true);
+    }
+    const int64_t l1 = h->launches;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wnode = nullptr;
+    if (!e && !s) e = cudaGraphAddNode(&wnode, g, tail.data(), nullptr, tail.size(), &np);
+    // the loop body: rounds 2, 3, ... (single-phase rounds; the round number is read on the device)
+    if (!e && !s) e = cudaStreamBeginCaptureToGraph(st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (!e && !s) {
+        round_body(2);
+        e = end_capture(np.conditional.phGraph_out[0], false);
+    }
+    const int64_t l2 = h->launches;
+    // after the loop: every instance's graph to its own arrays
+    if (!e && !s) e = cudaStreamBeginCaptureToGraph(st, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+    if (!e && !s) {
+        const int64_t nK = sb.npts * sb.K;
+        export_kernel<<<(unsigned)((nK + T - 1) / T), T, 0, st>>>(sl.idx, sl.key, sb.npts, sb.K, h->iv, sb.oidx,
+                                                                  sb.okey);
+        h->launches += 1;
+        e = end_capture(g, false);
+    }
+    if (!e && !s) e = cudaGraphInstantiate(&sb.exec, g, 0);
+    cudaGraphDestroy(g);
+    sb.launches_outer = (l1 - l0) + (h->launches - l2);
+    sb.launches_round = l2 - l1;
+    h->launches = l0;
+    h->rounds_run = r0;
+    if (s) return s;
+    if (e) {
+        (void)cudaGetLastError();
+        sb.exec = nullptr;
+        return status_of(e);
     }
     return KNND_OK;
 }
@@ -317,7 +428,7 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
     if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
     if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_INNER) return KNND_EINVAL;
     if (prm.loop < KNND_LOOP_AUTO || prm.loop > KNND_LOOP_GRAPH) return KNND_EINVAL;
-    if (prm.timing) prm.timing = 0;  // phase timing is a single-instance feature
+    prm.timing = 0;  // phase timing is a single-instance feature (events cannot sit in the loop body)
     const bool mixed = precision != KNND_PREC_FP64;
     for (int32_t i = 0; i < count; ++i) {
         const knnd_instance &in = inst[i];
@@ -327,9 +438,6 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
         if (in.K < 2 || in.K > KNND_MAX_K || (int64_t)in.K >= in.n) return KNND_EINVAL;
     }
     if (workspace_limit <= 0) workspace_limit = (int64_t)32 << 30;
-    // classes by (m, K); sub-batches within the budget, in input order
-    std::map<std::pair<int32_t, int32_t>, std::vector<int32_t>> classes;
-    for (int32_t i = 0; i < count; ++i) classes[{inst[i].m, inst[i].K}].push_back(i);
     knnd_batch *b = new (std::nothrow) knnd_batch();
     if (!b) return KNND_ENOMEM;
     b->inst.assign(inst, inst + count);
@@ -337,20 +445,23 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
     b->prec = precision;
     b->prm = prm;
     b->stream = (cudaStream_t)stream;
-    Caps caps = {0, 0, 0, 0, 0};
+    // classes by (m, K); sub-batches within the budget, in input order
+    std::map<std::pair<int32_t, int32_t>, std::vector<int32_t>> classes;
+    for (int32_t i = 0; i < count; ++i) classes[{inst[i].m, inst[i].K}].push_back(i);
+    int64_t largest = 0;  // bytes of the largest sub-batch
     for (auto &kv : classes) {
         const int32_t m = kv.first.first, K = kv.first.second;
         const int64_t bpp = bytes_per_point(m, K, mixed, prm.incremental != 0);
-        SubBatch cur{m, K, {}, 0};
+        SubBatch cur{};
+        cur.m = m;
+        cur.K = K;
         auto flush = [&]() {
             if (cur.members.empty()) return;
-            caps.n = std::max(caps.n, cur.npts);
-            caps.tab = std::max(caps.tab, cur.npts * pad_coords(m));
-            caps.nK = std::max(caps.nK, cur.npts * K);
-            caps.bucket = std::max(caps.bucket, cur.npts * K * (2 * (int64_t)K + 1));
-            caps.ninst = std::max(caps.ninst, (int32_t)cur.members.size());
+            largest = std::max(largest, cur.npts * bpp);
             b->subs.push_back(cur);
-            cur = SubBatch{m, K, {}, 0};
+            cur = SubBatch{};
+            cur.m = m;
+            cur.K = K;
         };
         for (int32_t i : kv.second) {
             const int64_t ni = inst[i].n;
@@ -359,39 +470,59 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
             if (!cur.members.empty() && over) flush();
             cur.members.push_back(i);
             cur.npts += ni;
+            cur.work += (double)ni * K * (2.0 * K + 1.0);
         }
         flush();
     }
-    const int32_t R = prm.max_rounds, ni = caps.ninst;
-    b->ninst_cap = ni;
-    knnd_status s = make_handle(&b->h, caps, dtype, precision, prm, stream);
-    if (!s) s = balloc(&b->idx, caps.nK);
-    if (!s) s = balloc(&b->key, caps.nK);
-    if (!s) s = balloc(&b->ptrs, ni);
-    if (!s) s = balloc(&b->lds, ni);
-    if (!s) s = balloc(&b->oidx, ni);
-    if (!s) s = balloc(&b->okey, ni);
-    if (!s) s = balloc(&b->hs.upd, (int64_t)ni * R);
-    if (!s) s = balloc(&b->hs.hits, (int64_t)ni * (R + 1));
-    if (!s) s = balloc(&b->hs.rescored, ni);
-    if (!s) s = balloc(&b->hs.fallback, ni);
-    if (!s) s = balloc(&b->hs.rounds, ni);
-    if (!s) s = balloc(&b->hs.reason, ni);
-    if (!s) s = balloc(&b->hs.nactive, 1);
-    if (!s) s = halloc(&b->h_base, ni + 1);
-    if (!s) s = halloc(&b->h_n, ni);
-    if (!s) s = halloc(&b->h_seed, ni);
-    if (!s) s = halloc(&b->h_ptrs, ni);
-    if (!s) s = halloc(&b->h_lds, ni);
-    if (!s) s = halloc(&b->h_oidx, ni);
-    if (!s) s = halloc(&b->h_okey, ni);
-    if (!s) s = halloc(&b->h_nactive, 1);
-    if (!s) s = halloc(&b->h_upd, (int64_t)ni * R);
-    if (!s) s = halloc(&b->h_hits, (int64_t)ni * (R + 1));
-    if (!s) s = halloc(&b->h_resc, ni);
-    if (!s) s = halloc(&b->h_fb, ni);
-    if (!s) s = halloc(&b->h_rounds, ni);
-    if (!s) s = halloc(&b->h_reason, ni);
+    // slots: as many as sub-batches, at most kMaxSlots, and as many workspaces of the
+    // largest sub-batch's size as 85 % of the free device memory holds
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_b = 0;
+    }
+    int nslots = std::min<int>(kMaxSlots, (int)b->subs.size());
+    if (largest > 0) nslots = std::min<int64_t>(nslots, std::max<int64_t>(1, (int64_t)(0.85 * free_b) / largest));
+    b->slots.resize(std::max(1, nslots));
+    std::vector<int> order(b->subs.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->subs[x].work > b->subs[y].work; });
+    for (int j : order) {  // largest first, to the least loaded slot
+        int best = 0;
+        for (int t = 1; t < (int)b->slots.size(); ++t)
+            if (b->slots[t].work < b->slots[best].work) best = t;
+        b->subs[j].slot = best;
+        b->slots[best].work += b->subs[j].work;
+        b->slots[best].subs.push_back(j);
+    }
+    knnd_status s = cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) == cudaSuccess ? KNND_OK : KNND_ECUDA;
+    for (Slot &sl : b->slots) {
+        if (s) break;
+        std::sort(sl.subs.begin(), sl.subs.end());  // input order within a slot
+        Caps caps = {0, 0, 0, 0, 0};
+        for (int j : sl.subs) {
+            const SubBatch &sb = b->subs[j];
+            caps.n = std::max(caps.n, sb.npts);
+            caps.tab = std::max(caps.tab, sb.npts * pad_coords(sb.m));
+            caps.nK = std::max(caps.nK, sb.npts * sb.K);
+            caps.bucket = std::max(caps.bucket, sb.npts * sb.K * (2 * (int64_t)sb.K + 1));
+            caps.ninst = std::max(caps.ninst, (int32_t)sb.members.size());
+        }
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            s = KNND_ECUDA;
+            break;
+        }
+        s = make_handle(&sl.h, caps, dtype, precision, prm, sl.stream);
+        if (!s) s = balloc(&sl.idx, caps.nK);
+        if (!s) s = balloc(&sl.key, caps.nK);
+        if (!s) b->ws_bytes += sl.h->ws_bytes + caps.nK * 12;
+    }
+    for (SubBatch &sb : b->subs) {
+        if (s) break;
+        s = make_sub_tables(b, sb);
+    }
     if (s) {
         batch_free(b);
         return s;
@@ -403,9 +534,79 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
 knnd_status knnd_batch_run(knnd_batch *b, knnd_build_info *info)
 {
     if (!b) return KNND_EINVAL;
-    for (const SubBatch &sb : b->subs) {
-        knnd_status s = run_sub(b, sb, info);
-        if (s) return s;
+    // every slot starts after the work already on the caller's stream
+    cudaError_t e = cudaEventRecord(b->start, b->stream);
+    for (Slot &sl : b->slots)
+        if (!e) e = cudaStreamWaitEvent(sl.stream, b->start, 0);
+    if (e) return status_of(e);
+    // one graph launch per sub-batch; slots take turns so that every stream gets work early
+    knnd_status s = KNND_OK;
+    size_t most = 0;
+    for (const Slot &sl : b->slots) most = std::max(most, sl.subs.size());
+    for (size_t k = 0; k < most && !s; ++k) {
+        for (Slot &sl : b->slots) {
+            if (k >= sl.subs.size()) continue;
+            SubBatch &sb = b->subs[sl.subs[k]];
+            if (!sb.exec) s = capture_sub(b, sb);
+            if (s) break;
+            e = cudaGraphLaunch(sb.exec, sl.stream);
+            if (e) {
+                s = status_of(e);
+                break;
+            }
+        }
+    }
+    // the caller's stream waits for every slot; the host for everything
+    for (Slot &sl : b->slots) {
+        cudaEventRecord(sl.done, sl.stream);
+        cudaStreamWaitEvent(b->stream, sl.done, 0);
+    }
+    for (Slot &sl : b->slots) {
+        const cudaError_t c = cudaStreamSynchronize(sl.stream);
+        if (c && !s) s = status_of(c);
+    }
+    if (s) return s;
+    for (Slot &sl : b->slots) {
+        const knnd_status t = take_error(sl.h);
+        if (t && !s) s = t;
+    }
+    if (s) return s;
+    const int32_t R = b->prm.max_rounds;
+    std::vector<int64_t> upd, hits, resc, fb;
+    std::vector<int32_t> rounds, reason;
+    for (SubBatch &sb : b->subs) {
+        const int32_t ni = (int32_t)sb.members.size();
+        rounds.resize(ni);
+        e = cudaMemcpy(rounds.data(), sb.hs.rounds, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost);
+        if (e) return status_of(e);
+        int32_t rmax = 0;
+        for (int32_t r : rounds) rmax = std::max(rmax, r);
+        b->launches += sb.launches_outer + (int64_t)std::max(0, rmax - 1) * sb.launches_round;
+        if (!info) continue;
+        upd.resize((size_t)ni * R);
+        hits.resize((size_t)ni * (R + 1));
+        resc.resize(ni);
+        fb.resize(ni);
+        reason.resize(ni);
+        e = cudaMemcpy(upd.data(), sb.hs.upd, sizeof(int64_t) * ni * R, cudaMemcpyDeviceToHost);
+        if (!e) e = cudaMemcpy(hits.data(), sb.hs.hits, sizeof(int64_t) * ni * (R + 1), cudaMemcpyDeviceToHost);
+        if (!e) e = cudaMemcpy(resc.data(), sb.hs.rescored, sizeof(int64_t) * ni, cudaMemcpyDeviceToHost);
+        if (!e) e = cudaMemcpy(fb.data(), sb.hs.fallback, sizeof(int64_t) * ni, cudaMemcpyDeviceToHost);
+        if (!e) e = cudaMemcpy(reason.data(), sb.hs.reason, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost);
+        if (e) return status_of(e);
+        for (int32_t j = 0; j < ni; ++j) {
+            const knnd_instance &in = b->inst[sb.members[j]];
+            knnd_build_info &o = info[sb.members[j]];
+            std::memset(&o, 0, sizeof(o));
+            o.rounds = rounds[j];
+            o.stop_reason = reason[j];
+            for (int32_t r = 0; r < o.rounds; ++r) o.updates[r] = upd[(size_t)j * R + r];
+            for (int32_t r = 0; r <= o.rounds; ++r) o.fcc_hits[r] = hits[(size_t)j * (R + 1) + r];
+            o.init_pairs = in.n * in.K;
+            o.proposals = (int64_t)o.rounds * in.n * in.K * (2 * (int64_t)in.K + 1);
+            o.rescored = resc[j];
+            o.merge_fallbacks = fb[j];
+        }
     }
     return KNND_OK;
 }
@@ -415,14 +616,16 @@ knnd_status knnd_batch_info(const knnd_batch *b, int32_t *sub_batches, int64_t *
 {
     if (!b) return KNND_EINVAL;
     if (sub_batches) *sub_batches = (int32_t)b->subs.size();
-    if (workspace_bytes) *workspace_bytes = b->h ? b->h->ws_bytes : 0;
-    if (kernel_launches) *kernel_launches = b->h ? b->h->launches : 0;
+    if (workspace_bytes) *workspace_bytes = b->ws_bytes;
+    if (kernel_launches) *kernel_launches = b->launches;
     return KNND_OK;
 }
 
 void knnd_batch_destroy(knnd_batch *b)
 {
     if (!b) return;
+    for (Slot &sl : b->slots)
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
     cudaStreamSynchronize(b->stream);
     batch_free(b);
 }

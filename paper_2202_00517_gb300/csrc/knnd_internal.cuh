@@ -281,7 +281,8 @@ namespace knnd {
 cudaError_t launch_precompute(knnd_handle *h, const void *points, int64_t ld);
 cudaError_t launch_precompute_from(knnd_handle *h, const void *points, int64_t ld, const void *const *ptrs,
                                    const int64_t *lds);
-cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round);
+// round_dev: the round number is read on the device there (a device-driven loop), else `round`.
+cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round, const int32_t *round_dev = nullptr);
 cudaError_t launch_init_graph(knnd_handle *h, uint64_t seed, int32_t *idx, double *key, uint8_t *newflag);
 cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double *key);
 cudaError_t launch_thresholds(knnd_handle *h, const int32_t *idx, const double *key);

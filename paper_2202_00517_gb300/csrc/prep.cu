@@ -268,8 +268,9 @@ __global__ void fcc_kernel(const int32_t *__restrict__ idx, int64_t n, int K, ui
 // stream (seed_i, s, round, kTagFcc) over its local indices; hits go to the
 // instance's counter.  Stopped instances draw nothing.
 __global__ void fcc_batch_kernel(const int32_t *__restrict__ idx, int K, InstView iv, int32_t ninst, int32_t round,
-                                 int32_t S, int32_t *err)
+                                 int32_t S, int32_t *err, const int32_t *round_dev)
 {
+    if (round_dev) round = *round_dev;  // a round of a device-driven loop
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)ninst * S) return;
     const int i = (int)(t / S);
@@ -291,12 +292,12 @@ __global__ void fcc_batch_kernel(const int32_t *__restrict__ idx, int K, InstVie
         atomicAdd((unsigned long long *)&iv.cnt[(int64_t)i * kCntNum + kCntHits], 1ull);
 }
 
-cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round)
+cudaError_t launch_fcc_batch(knnd_handle *h, const int32_t *idx, int32_t round, const int32_t *round_dev)
 {
     const int threads = 256;
     const int64_t total = (int64_t)h->ninst * h->prm.fcc_samples;
     fcc_batch_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, h->stream>>>(
-        idx, h->K, h->iv, h->ninst, round, h->prm.fcc_samples, h->err);
+        idx, h->K, h->iv, h->ninst, round, h->prm.fcc_samples, h->err, round_dev);
     h->launches += 1;
     return cudaGetLastError();
 }
