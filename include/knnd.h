@@ -96,6 +96,13 @@ typedef struct {
                                      updates, Dong et al.'s delta-proportion rule (Sec. 2, Table 1) (0) */
     int32_t comparator;           /* KNND_CMP_*: how x ranks the other points (KNND_CMP_KL) */
     int32_t loop;                 /* KNND_LOOP_*: how knnd_build runs its rounds (KNND_LOOP_AUTO) */
+    /* Execution choices that change the speed, never the result (0: the value the
+     * committed tuning table gives for the shape's padded m and K): */
+    int32_t split_den;            /* round 1 first runs the hubs [0, n / split_den) and merges them, so that
+                                     the rest propose against tighter thresholds (2..64); 1: one phase */
+    int32_t merge_keep;           /* candidates each lane of the merge's fast path keeps (4 or 8; K <= 32) */
+    int32_t join_blocks;          /* resident 128-thread blocks per SM of the FP32 TMA join (1..8; at most
+                                     what fits) */
 } knnd_params;
 
 /* The round loop of knnd_build.  Both give the same graph and report. */

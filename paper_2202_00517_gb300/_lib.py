@@ -56,7 +56,8 @@ class knnd_params(ctypes.Structure):
     _fields_ = [("fcc_samples", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("stop_on_zero_updates", ctypes.c_int32), ("debug", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("incremental", ctypes.c_int32), ("stop_delta", ctypes.c_float),
-                ("comparator", ctypes.c_int32), ("loop", ctypes.c_int32)]
+                ("comparator", ctypes.c_int32), ("loop", ctypes.c_int32), ("split_den", ctypes.c_int32),
+                ("merge_keep", ctypes.c_int32), ("join_blocks", ctypes.c_int32)]
 
 
 class knnd_build_info(ctypes.Structure):

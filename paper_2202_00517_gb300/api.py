@@ -57,13 +57,14 @@ class Handle:
     def __init__(self, n: int, m: int, K: int, dtype="f32", precision="mixed", fcc_samples: int = 10000,
                  max_rounds: int = 64, stop_on_zero_updates: bool = True, debug: bool = False,
                  timing: bool = False, incremental: bool = False, stop_delta: float = 0.0, comparator: str = "kl",
-                 loop: str = "auto", stream=None):
+                 loop: str = "auto", stream=None, split_den: int = 0, merge_keep: int = 0, join_blocks: int = 0):
         lib = _lib.load()
         self.n, self.m, self.K = n, m, K
         self.dtype = _DTYPE[dtype]
         self.torch_dtype = torch.float32 if self.dtype == _lib.KNND_F32 else torch.float64
         prm = _lib.knnd_params(fcc_samples, max_rounds, int(stop_on_zero_updates), int(debug), int(timing),
-                               int(incremental), float(stop_delta), _CMP[comparator], _LOOP[loop])
+                               int(incremental), float(stop_delta), _CMP[comparator], _LOOP[loop], int(split_den),
+                               int(merge_keep), int(join_blocks))
         h = ctypes.c_void_p()
         check(lib.knnd_create(ctypes.byref(h), n, m, K, self.dtype, _PREC[precision], ctypes.byref(prm),
                               _stream_ptr(stream)), "knnd_create")
@@ -180,7 +181,7 @@ def build(points, K: int, seed: int = 0, precision: str = "mixed", **kw) -> dict
 def build_batched(points_list, Ks, seeds, precision: str = "mixed", fcc_samples: int = 10000,
                   max_rounds: int = 64, stop_on_zero_updates: bool = True, workspace_limit: int = 0,
                   incremental: bool = False, stop_delta: float = 0.0, comparator: str = "kl", stream=None,
-                  outputs=None):
+                  outputs=None, split_den: int = 0, merge_keep: int = 0, join_blocks: int = 0):
     """Batched form: build many independent instances together.
 
     points_list: CUDA tensors (n_i x m_i, one dtype for all); Ks, seeds: per instance.
@@ -208,7 +209,8 @@ def build_batched(points_list, Ks, seeds, precision: str = "mixed", fcc_samples:
         outs.append((idx, key))
         arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, K, sd, idx.data_ptr(), key.data_ptr())
     prm = _lib.knnd_params(fcc_samples, max_rounds, int(stop_on_zero_updates), 0, 0, int(incremental),
-                           float(stop_delta), _CMP[comparator])
+                           float(stop_delta), _CMP[comparator], _lib.KNND_LOOP_AUTO, int(split_den), int(merge_keep),
+                           int(join_blocks))
     infos = (_lib.knnd_build_info * count)()
     check(lib.knnd_build_batched(count, ctypes.cast(arr, ctypes.c_void_p), dtype, _PREC[precision],
                                  ctypes.byref(prm), workspace_limit, ctypes.cast(infos, ctypes.c_void_p),

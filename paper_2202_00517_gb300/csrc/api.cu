@@ -140,7 +140,7 @@ knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
 
 // Split first round.  Round 1 proposes nearly its whole pool (the K-th of K
 // random friends is a poor threshold), so it runs in two phases: the hubs
-// [0, n / kSplitDen) propose and their candidates are merged into a copy of the
+// [0, n / split_den) propose and their candidates are merged into a copy of the
 // graph; every row's K-th entry there is an upper bound of its K-th key at the
 // end of the round (any part of the pool gives one), so the remaining hubs
 // propose against that tighter threshold, and their candidates are merged into
@@ -148,8 +148,7 @@ knnd_status do_prepare(knnd_handle *h, const void *points, int64_t ld)
 // the one-phase round: the same pool, the same K best.  Measured: 3 % (n = 1e6,
 // m = 21, K = 20) to 5 % (m = 65, K = 32) off a build; splitting later rounds,
 // whose thresholds are already good, cost more than it saved.
-constexpr int32_t kSplitRounds = 1;
-constexpr int64_t kSplitDen = 8;
+constexpr int32_t kSplitRounds = 1;  // the share of the first phase, 1 / split_den, comes from the tuning
 
 // G_{r-1} -> G_r in place; the device counters accumulate.  loop: a round of
 // the device-driven loop (the FCC sample reads seed and round there).
@@ -161,15 +160,16 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
     h->round_flag = (h->prm.incremental && newflag) ? newflag : nullptr;
     // one instance: the hubs [0, n / den) then the rest; several instances
     // (batched form): each instance's first n_i / den hubs, then the rest
-    const bool split = h->idxA && round >= 1 && round <= kSplitRounds;
+    const int64_t den = h->split_den;
+    const bool split = h->idxA && round >= 1 && round <= kSplitRounds && den >= 2;
     const bool by_phase = split && h->iv.of;
-    const int64_t hs = !split ? h->n : (by_phase ? h->n : std::max<int64_t>(1, h->n / kSplitDen));
+    const int64_t hs = !split ? h->n : (by_phase ? h->n : std::max<int64_t>(1, h->n / den));
     int t = phase_begin(h, KNND_PHASE_CSR);
     cudaError_t e = launch_reverse_csr(h, idx, key);
     phase_end(h, t, KNND_PHASE_CSR);
     if (e == cudaSuccess) {
         t = phase_begin(h, KNND_PHASE_JOIN);
-        e = launch_join(h, idx, 0, hs, by_phase ? 1 : 0, (int)kSplitDen);
+        e = launch_join(h, idx, 0, hs, by_phase ? 1 : 0, (int)den);
         phase_end(h, t, KNND_PHASE_JOIN);
     }
     if (e == cudaSuccess) {
@@ -184,7 +184,7 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
         phase_end(h, t, KNND_PHASE_CSR);
         if (e == cudaSuccess) {
             t = phase_begin(h, KNND_PHASE_JOIN);
-            e = by_phase ? launch_join(h, idx, 0, h->n, 2, (int)kSplitDen) : launch_join(h, idx, hs, h->n);
+            e = by_phase ? launch_join(h, idx, 0, h->n, 2, (int)den) : launch_join(h, idx, hs, h->n);
             phase_end(h, t, KNND_PHASE_JOIN);
         }
         if (e == cudaSuccess) {
@@ -399,6 +399,9 @@ knnd_params default_params()
     p.stop_delta = 0.f;
     p.comparator = KNND_CMP_KL;
     p.loop = KNND_LOOP_AUTO;
+    p.split_den = 0;
+    p.merge_keep = 0;
+    p.join_blocks = 0;
     return p;
 }
 
@@ -416,6 +419,11 @@ void configure(knnd_handle *h, int64_t n, int32_t m, int32_t K)
         h->bound_c = bound_c_bf16x3(h->MP);
     h->bucket_cap = n * K * (2 * (int64_t)K + 1);
     h->prepared = false;
+    // execution choices: the caller's, else the committed tuning table's for (MP, K)
+    const TuneEntry t = tune_lookup(h->MP, K);
+    h->split_den = h->prm.split_den > 0 ? h->prm.split_den : t.split_den;
+    h->merge_keep = h->prm.merge_keep > 0 ? h->prm.merge_keep : t.merge_keep;
+    h->join_blocks = h->prm.join_blocks > 0 ? h->prm.join_blocks : t.join_blocks;
 }
 
 knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd_precision precision,
@@ -561,6 +569,7 @@ knnd_status knnd_create(knnd_handle **out, int64_t n, int32_t m, int32_t K, knnd
     if (prm.debug < 0 || prm.debug > 2) return KNND_EINVAL;
     if (prm.loop < KNND_LOOP_AUTO || prm.loop > KNND_LOOP_GRAPH) return KNND_EINVAL;
     if (prm.loop == KNND_LOOP_GRAPH && prm.timing) return KNND_EINVAL;  // event nodes cannot sit in the loop body
+    if (!knnd::tuning_valid(prm)) return KNND_EINVAL;
     // bucket capacity n*K*(2K+1) and CSR sizes use int64; the per-row slot counter is int32
     if ((int64_t)K * K + (int64_t)(K + 1) * (n - 1) >= ((int64_t)1 << 31)) return KNND_EOVERFLOW;
     knnd::Caps caps;

@@ -428,6 +428,7 @@ knnd_status knnd_batch_create(knnd_batch **out, int32_t count, const knnd_instan
     if (!(prm.stop_delta >= 0.f && prm.stop_delta <= 1.f)) return KNND_EINVAL;
     if (prm.comparator < KNND_CMP_KL || prm.comparator > KNND_CMP_INNER) return KNND_EINVAL;
     if (prm.loop < KNND_LOOP_AUTO || prm.loop > KNND_LOOP_GRAPH) return KNND_EINVAL;
+    if (!tuning_valid(prm)) return KNND_EINVAL;
     prm.timing = 0;  // phase timing is a single-instance feature (events cannot sit in the loop body)
     const bool mixed = precision != KNND_PREC_FP64;
     for (int32_t i = 0; i < count; ++i) {

@@ -556,6 +556,7 @@ cudaError_t run_tma(knnd_handle *h, const TmaJoinArgs &a)
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (per_sm < 1) per_sm = 1;
+    if (h->join_blocks > 0) per_sm = std::min(per_sm, h->join_blocks);  // the tuned occupancy, if lower
     const int64_t need = (a.h_hi - a.h_lo + threads / 32 - 1) / (threads / 32);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)h->num_sms * per_sm));
     kern<<<(unsigned)grid, threads, smem, h->stream>>>(a);

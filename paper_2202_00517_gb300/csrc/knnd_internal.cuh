@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "../../include/knnd.h"
+#include "tune_table.h"
 
 namespace knnd {
 
@@ -185,6 +186,8 @@ struct knnd_handle {
     int num_sms;
     int fail_alloc_at;  // > 0: the fail_alloc_at-th workspace allocation fails (KNND_TEST_FAIL_ALLOC)
     int join_lsu;       // 1: the mixed join gathers with plain loads even where the TMA form applies (KNND_JOIN=lsu)
+    // execution choices for the current shape (params, else the tuning table)
+    int split_den, merge_keep, join_blocks;
     int allocs;
     bool prepared;
 
@@ -321,6 +324,21 @@ knnd_status take_error(knnd_handle *h);
 knnd_status round_ops(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx, double *key, uint8_t *newflag,
                       int64_t *fcc_hits);
 knnd_status status_of(cudaError_t e);
+
+// The tuning table's entry for a shape (kTuneDefault when none covers it).
+inline TuneEntry tune_lookup(int MP, int K)
+{
+    for (const TuneEntry &t : kTuneTable)
+        if (t.MP == MP && K >= t.K_lo && K <= t.K_hi) return t;
+    return kTuneDefault;
+}
+
+// Range checks of the execution choices of knnd_params (0: from the table).
+inline bool tuning_valid(const knnd_params &p)
+{
+    return p.split_den >= 0 && p.split_den <= 64 && (p.merge_keep == 0 || p.merge_keep == 4 || p.merge_keep == 8) &&
+           p.join_blocks >= 0 && p.join_blocks <= 8;
+}
 
 inline int pad_coords(int m) {
     int mp = (m + 7) / 8 * 8;

@@ -827,7 +827,13 @@ cudaError_t launch_merge_from(knnd_handle *h, const int32_t *in_idx, const doubl
     const bool kl_form = h->prm.comparator == KNND_CMP_KL || h->prm.comparator == KNND_CMP_INNER;
     const unsigned fgrid = (unsigned)h->num_sms * 2;
     // the FP64 form's keys come from the join (no re-score): one instance serves every comparator
-    if (h->K <= 32) {
+    if (h->K <= 32 && h->merge_keep == 8) {  // more candidates kept per lane: fewer rows need the second kernel
+        if (fp64) launch_merge_pair<1, 8, false, KNND_CMP_KL>(h, a, grid, fgrid, threads);
+        else if (kl_form) launch_merge_pair<1, 8, true, KNND_CMP_KL>(h, a, grid, fgrid, threads);
+        else if (h->prm.comparator == KNND_CMP_KL_REVERSE)
+            launch_merge_pair<1, 8, true, KNND_CMP_KL_REVERSE>(h, a, grid, fgrid, threads);
+        else launch_merge_pair<1, 8, true, KNND_CMP_SQEUCLIDEAN>(h, a, grid, fgrid, threads);
+    } else if (h->K <= 32) {
         if (fp64) launch_merge_pair<1, 4, false, KNND_CMP_KL>(h, a, grid, fgrid, threads);
         else if (kl_form) launch_merge_pair<1, 4, true, KNND_CMP_KL>(h, a, grid, fgrid, threads);
         else if (h->prm.comparator == KNND_CMP_KL_REVERSE)

@@ -42,9 +42,9 @@ def test_version_and_status_strings(lib):
 
 
 def test_struct_layouts():
-    # host structs of the header: eight int32 params and a float; build info 8 + 64*8 + 65*8 + 7*8 bytes;
+    # host structs of the header: eleven int32 params and a float; build info 8 + 64*8 + 65*8 + 7*8 bytes;
     # stats 3 int64 + 6 int64 + 6 double
-    assert ctypes.sizeof(_lib.knnd_params) == 36
+    assert ctypes.sizeof(_lib.knnd_params) == 48
     assert ctypes.sizeof(_lib.knnd_build_info) == 8 + 64 * 8 + 65 * 8 + 7 * 8
     assert ctypes.sizeof(_lib.knnd_stats) == 3 * 8 + 6 * 8 + 6 * 8
 
@@ -74,7 +74,11 @@ def test_create_rejects_bad_params(lib):
                 _lib.knnd_params(100, 10, 1, 0, 0, 0, -0.5), _lib.knnd_params(100, 10, 1, 0, 0, 0, 2.0),
                 _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 4),             # no such comparator
                 _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 3),         # no such loop
-                _lib.knnd_params(100, 10, 1, 0, 1, 0, 0.0, 0, _lib.KNND_LOOP_GRAPH)):  # graph loop with timing
+                _lib.knnd_params(100, 10, 1, 0, 1, 0, 0.0, 0, _lib.KNND_LOOP_GRAPH),  # graph loop with timing
+                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, 65),     # split share out of range
+                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, -1),
+                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, 0, 5),   # merge keeps 4 or 8
+                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, 0, 0, 9)):  # join blocks out of range
         assert lib.knnd_create(ctypes.byref(h), 1000, 6, 10, 0, 1, ctypes.byref(prm), None) == _lib.KNND_EINVAL
     assert lib.knnd_create(None, 1000, 6, 10, 0, 1, None, None) == _lib.KNND_EINVAL
 

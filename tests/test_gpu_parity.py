@@ -407,3 +407,34 @@ def test_bounded_wait_timeout_is_reported(knnd):
     r = ref.build(pts, seed)
     ref.close()
     assert torch.equal(out["idx"], r["idx"])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("n,m,K", [(20000, 21, 20), (6000, 11, 32), (8000, 6, 8)])
+@pytest.mark.parametrize("choice", [(1, 4, 0), (4, 8, 3), (16, 8, 1), (2, 4, 5)])
+def test_tuning_choices_same_graph(knnd, prec, n, m, K, choice):
+    # the execution choices of the tuning table (round 1's split share, the
+    # merge's per-lane keep, the TMA join's blocks per SM) change the speed only
+    seed = 5
+    pts = _dev(dirichlet_points(n, m, seed, np.float32))
+    ref = knnd.Handle(n, m, K, dtype="f32", precision=prec)
+    a = ref.build(pts, seed)
+    ref.close()
+    s, keep, blocks = choice
+    h = knnd.Handle(n, m, K, dtype="f32", precision=prec, split_den=s, merge_keep=keep, join_blocks=blocks)
+    b = h.build(pts, seed)
+    h.close()
+    assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"]
+    assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["key"], b["key"])
+
+
+def test_tuning_choices_batched_same_graphs(knnd):
+    shapes = [(3000, 6, 8), (5000, 11, 16), (4000, 21, 32), (700, 21, 20)]
+    pts = [_dev(dirichlet_points(n, m, 40 + i, np.float32)) for i, (n, m, K) in enumerate(shapes)]
+    Ks = [K for _, _, K in shapes]
+    seeds = [900 + i for i in range(len(shapes))]
+    a = knnd.build_batched(pts, Ks, seeds)
+    b = knnd.build_batched(pts, Ks, seeds, split_den=1, merge_keep=8, join_blocks=2)
+    for x, y in zip(a, b):
+        assert x["rounds"] == y["rounds"] and x["updates"] == y["updates"]
+        assert torch.equal(x["idx"], y["idx"]) and torch.equal(x["key"], y["key"])
