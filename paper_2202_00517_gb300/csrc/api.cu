@@ -48,7 +48,7 @@ void free_all(knnd_handle *h)
     void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg, h->slot,
                     h->heavy_items, h->heavy_nitems,
                     h->cof_off, h->cof, h->cof_new, h->flag_tmp, h->scan_tmp, h->tau, h->idxK, h->meta, h->Ex, h->bcnt, h->bkey,
-                    h->bent, h->fb_list, h->fb_T, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev, h->idxA, h->keyA,
+                    h->bent, h->fb_list, h->fb_T, h->join_queue, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev, h->idxA, h->keyA,
                     h->flagA,
                     h->inst_of, h->inst_base, h->inst_n, h->inst_seed, h->inst_active, h->inst_cnt};
     for (void *p : ptrs)
@@ -475,6 +475,7 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
     if (!s && !mixed) s = dalloc(h, &h->bkey, c.bucket);
     if (!s) s = dalloc(h, &h->fb_list, n);
     if (!s) s = dalloc(h, &h->fb_T, n);
+    if (!s) s = dalloc(h, &h->join_queue, 1);
     if (!s) s = dalloc(h, &h->fb_count, 1);
     if (!s) s = dalloc(h, &h->cnt, kCntNum);
     if (!s) s = dalloc(h, &h->idxA, c.nK);  // the split first round's graph copy

@@ -15,6 +15,9 @@
 //    rows of a two-dimensional tensor map per instruction, one row high), which
 //    moves them into shared memory without passing through the load/store
 //    pipe; an index outside the table (an empty row slot) reads zeros;
+//  * the kernel is persistent (as many blocks as fit on the SMs); its warps take
+//    hubs from a device work queue, chunks of consecutive hubs claimed by an
+//    atomic counter, so the load spreads by what each hub costs;
 //  * the copies of the next item are issued as soon as the current item's rows
 //    have left the staging buffer, and the ids of the item after it are loaded
 //    while the current item is scored, so gathers, id chases and scoring of
@@ -60,6 +63,7 @@ struct TmaJoinArgs {
     int32_t *err;
     int debug;
     InstView iv;
+    unsigned long long *queue;  // the work queue's counter: hubs claimed so far (zeroed per launch)
     float col_scale;
     double col_inv;
     // bound audit (debug, comparators without a column offset): the FP64
@@ -153,12 +157,27 @@ struct Item {
     bool valid;
 };
 
-// The warp's walk over its hubs h_lo + first, + stride, ...: the next hub to
-// consider and its co-friend offsets, loaded one hub ahead of their use.
+// The warp's walk over the hubs it takes from the launch's work queue: chunks
+// of kChunk consecutive hubs of [h_lo, h_hi), each claimed by one atomicAdd on
+// the queue counter as the warp reaches it, so warps that meet cheap hubs take
+// more of them.  `next` is the next hub to consider; its co-friend offsets are
+// loaded one hub ahead of their use.
+constexpr int kChunk = 32;
+
 struct HubWalk {
-    int64_t next;
-    int64_t c0, c1;  // cof_off[next], cof_off[next + 1] (when next < h_hi)
+    int64_t next, end;  // the claimed chunk [next, end)
+    int64_t c0, c1;     // cof_off[next], cof_off[next + 1] (when next < h_hi)
 };
+
+// Called by all lanes of the warp together.
+__device__ __forceinline__ void walk_claim(const TmaJoinArgs &a, HubWalk &w)
+{
+    unsigned long long t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(a.queue, (unsigned long long)kChunk);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    w.next = a.h_lo + (int64_t)t;
+    w.end = min(w.next + kChunk, a.h_hi);
+}
 
 __device__ __forceinline__ void walk_load(const TmaJoinArgs &a, HubWalk &w)
 {
@@ -168,9 +187,16 @@ __device__ __forceinline__ void walk_load(const TmaJoinArgs &a, HubWalk &w)
     }
 }
 
+__device__ __forceinline__ void walk_step(const TmaJoinArgs &a, HubWalk &w)
+{
+    w.next += 1;
+    if (w.next >= w.end) walk_claim(a, w);
+    walk_load(a, w);
+}
+
 // The item after `it`: the hub's next 32 rows, or the first rows of the
 // warp's next hub that is live and in the launch's phase.
-__device__ __forceinline__ Item next_item(const TmaJoinArgs &a, Item it, HubWalk &w, int64_t stride)
+__device__ __forceinline__ Item next_item(const TmaJoinArgs &a, Item it, HubWalk &w)
 {
     if (it.valid && (it.ch + 1) * 32 < it.nrows) {
         it.ch += 1;
@@ -183,16 +209,14 @@ __device__ __forceinline__ Item next_item(const TmaJoinArgs &a, Item it, HubWalk
     while (w.next < a.h_hi) {
         const int64_t v = w.next;
         if (!a.iv.live(v) || !in_phase(a.iv, a.phase, a.split_den, a.n, v)) {
-            w.next += stride;
-            walk_load(a, w);
+            walk_step(a, w);
             continue;
         }
         r.v = v;
         r.c0 = w.c0;
         r.nrows = a.K + (int)(w.c1 - w.c0);
         r.valid = true;
-        w.next += stride;
-        walk_load(a, w);  // in flight until the warp's next hub
+        walk_step(a, w);  // the next hub's offsets in flight until the warp reaches it
         break;
     }
     return r;
@@ -247,7 +271,7 @@ __global__ void __launch_bounds__(128, MP <= 24 ? 5 : 4) join_tma_kernel(const _
 {
     extern __shared__ __align__(128) unsigned char smem_tma[];
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = a.K;
     const TmaLayout L(MP, K, COL);
     long long ndot = 0, nviol = 0;
@@ -274,10 +298,9 @@ __global__ void __launch_bounds__(128, MP <= 24 ? 5 : 4) join_tma_kernel(const _
     }
     __syncwarp();
 
-    const int64_t stride = (int64_t)gridDim.x * wpb;
     HubWalk walk;
-    walk.next = a.h_lo + (int64_t)blockIdx.x * wpb + warp;
     walk.c0 = walk.c1 = 0;
+    walk_claim(a, walk);
     walk_load(a, walk);
     Item none;
     none.valid = false;
@@ -326,10 +349,10 @@ __global__ void __launch_bounds__(128, MP <= 24 ? 5 : 4) join_tma_kernel(const _
     };
 
     // prologue: item A's copies in flight, item B's ids loading
-    Item A = next_item(a, none, walk, stride);
+    Item A = next_item(a, none, walk);
     if (!A.valid) return;
     int ridA = check_id(a, load_id(a, A, lane), has_row(A, lane));
-    Item B = next_item(a, A, walk, stride);
+    Item B = next_item(a, A, walk);
     int ridB = load_id(a, B, lane);
     int slotA = 0;
     issue(A, ridA, slotA);
@@ -364,7 +387,7 @@ __global__ void __launch_bounds__(128, MP <= 24 ? 5 : 4) join_tma_kernel(const _
         ridB = check_id(a, ridB, has_row(B, lane));
         if (B.valid) issue(B, ridB, slotB);
         // 3. item C's ids and item B's row records, in flight while A is scored
-        const Item C = next_item(a, B, walk, stride);
+        const Item C = next_item(a, B, walk);
         const int ridC = load_id(a, C, lane);
         RowMeta mB;
         mB.phi = 0.f;
@@ -596,6 +619,8 @@ cudaError_t launch_join_tma(knnd_handle *h, const int32_t *idx, int64_t h_lo, in
     a.bcnt = h->bcnt;
     a.bent = h->bent;
     a.err = h->err;
+    a.queue = h->join_queue;
+    cudaMemsetAsync(h->join_queue, 0, sizeof(unsigned long long), h->stream);
     a.debug = h->prm.debug;
     a.iv = h->iv;
     a.col_scale = cmp == KNND_CMP_SQEUCLIDEAN ? 2.f : 1.f;

@@ -228,6 +228,7 @@ struct knnd_handle {
     // u = key rounded up to FP32.  FP64 form: the exact key at the same slot.
     int2 *bent;
     double *bkey;
+    unsigned long long *join_queue;  // the TMA join's work-queue counter
     int32_t *fb_list;   // n: rows the merge's fast path leaves to its second kernel
     int32_t *fb_count;
     double *fb_T;       // n: the bound T of each such row's K-th key
