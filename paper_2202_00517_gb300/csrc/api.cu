@@ -475,7 +475,7 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
     if (!s && !mixed) s = dalloc(h, &h->bkey, c.bucket);
     if (!s) s = dalloc(h, &h->fb_list, n);
     if (!s) s = dalloc(h, &h->fb_T, n);
-    if (!s) s = dalloc(h, &h->join_queue, 1);
+    if (!s) s = dalloc(h, &h->join_queue, 2);  // the join's and the merge's work-queue counters
     if (!s) s = dalloc(h, &h->fb_count, 1);
     if (!s) s = dalloc(h, &h->cnt, kCntNum);
     if (!s) s = dalloc(h, &h->idxA, c.nK);  // the split first round's graph copy

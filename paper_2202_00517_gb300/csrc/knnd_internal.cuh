@@ -228,7 +228,7 @@ struct knnd_handle {
     // u = key rounded up to FP32.  FP64 form: the exact key at the same slot.
     int2 *bent;
     double *bkey;
-    unsigned long long *join_queue;  // the TMA join's work-queue counter
+    unsigned long long *join_queue;  // work-queue counters: [0] the TMA join's, [1] the merge's
     int32_t *fb_list;   // n: rows the merge's fast path leaves to its second kernel
     int32_t *fb_count;
     double *fb_T;       // n: the bound T of each such row's K-th key

@@ -157,6 +157,7 @@ struct MergeArgs {
     int32_t *fb_list;   // rows left to the second kernel
     int32_t *fb_count;
     double *fb_T;       // per row: the upper bound T of its K-th key the fast path found (K <= 32)
+    unsigned long long *queue;  // the work queue's counter: rows claimed so far (zeroed per launch)
     InstView iv;
 };
 
@@ -699,6 +700,8 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
 // CMP: the comparator (KNND_CMP_*) the mixed forms re-score with; the entries'
 // u orders candidates like key - ro(x), ro = negH(x) for KL, |x|^2 for squared
 // Euclidean, 0 for reverse KL.
+constexpr int kRowChunk = 16;
+
 template <int NE, int R, bool MIXED, int CMP>
 __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
 {
@@ -706,13 +709,27 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs a)
     __shared__ int2 s_live[8][32 * R];
     __shared__ BatchScratch s_batch[NE == 1 ? 8 : 1];
     const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
     const int K = a.K;
     int *tab = s_hash[threadIdx.x >> 5];
     int2 *live_list = s_live[threadIdx.x >> 5];
     int newcount = 0;
     long long rescored = 0, fallbacks = 0, survivors = 0;
-    for (int64_t x = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); x < a.n; x += (int64_t)gridDim.x * wpb) {
+    // rows from the work queue: chunks of kRowChunk consecutive rows, each claimed
+    // by one atomicAdd as the warp reaches it (rows differ widely in cost)
+    int64_t x = 0, xend = 0;
+    auto claim = [&]() {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.queue, (unsigned long long)kRowChunk);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        x = (int64_t)t;
+        xend = min(x + kRowChunk, a.n);
+    };
+    claim();
+    for (; x < a.n; ++x) {
+        if (x >= xend) {
+            claim();
+            if (x >= a.n) break;
+        }
         if (!a.iv.live(x)) continue;  // row of a stopped instance (batched form)
         WarpList<NE> X;
         load_row(a, x, lane, X);
@@ -820,6 +837,8 @@ cudaError_t launch_merge_from(knnd_handle *h, const int32_t *in_idx, const doubl
     a.fb_list = h->fb_list;
     a.fb_count = h->fb_count;
     a.fb_T = h->fb_T;
+    a.queue = h->join_queue + 1;
+    cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), h->stream);
     a.iv = h->iv;
     cudaMemsetAsync(h->fb_count, 0, sizeof(int32_t), h->stream);
     const bool fp64 = h->prec == KNND_PREC_FP64;
