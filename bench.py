@@ -140,13 +140,6 @@ def join_traffic_per_launch(name, source="join.cu", profile_prefix="join_mixed")
     return float(m_b.group(1))
 
 
-def tma_join_applies(m, k, comparator="kl"):
-    """The library's dispatch rule for the TMA-gathered FP32 join (mixed form,
-    up to 32 padded coordinates, K <= 32, no incremental proposals, not the inner
-    product): which kernel the roofline describes."""
-    return pad_m(m) <= 32 and k <= 32 and comparator != "inner" and os.environ.get("KNND_JOIN") != "lsu"
-
-
 FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz
 
 
@@ -408,7 +401,7 @@ def gpu_single(args, name, rank, world, local, barrier):
     # columns' logs), the friend and co-friend id lists, the co-friend offsets, the
     # 16-byte row records, and the 8-byte entries of the survivors written
     compulsory = 2.0 * N * MP * 4 + 2.0 * N * K * 4 + 8.0 * (N + 1) + 16.0 * N + 8.0 * surv_t / join_n
-    tma = args.form == "mixed" and tma_join_applies(M, K)
+    tma = info.get("join_kernel") == "tma"
     if tma:
         kname, traffic = f"join_tma_kernel<{MP}, 0, 0>", join_traffic_per_launch(name, "join_tma.cu", "join_tma")
     elif args.form == "mixed":
@@ -554,9 +547,9 @@ def gpu_leg(args, name, local, steps=2, warmup=1):
                      "rescored_per_build": r["rescored"],
                      "join_ms_per_launch": st["phase_ms"]["join"] / max(1, st["phase_count"]["join"]),
                      "merge_ms_per_launch": st["phase_ms"]["merge"] / max(1, st["phase_count"]["merge"]),
-                     "join_kernel": (f"join_tma_kernel<{pad_m(m)}, 0, 0>" if prec == "mixed" and tma_join_applies(m, k)
-                                     else (f"join_mixed_kernel<{pad_m(m)}, 0, 0, 0>" if prec == "mixed"
-                                           else f"join_tc_kernel<{pad_m(m)}>"))}
+                     "join_kernel": {"tma": f"join_tma_kernel<{pad_m(m)}, 0, 0>",
+                                     "plain": f"join_mixed_kernel<{pad_m(m)}, 0, 0, 0>",
+                                     "tc": f"join_tc_kernel<{pad_m(m)}>"}.get(r["join_kernel"], r["join_kernel"])}
     a, b = res["mixed"], res["bf16x3"]
     out["same_graph_bf16x3_vs_mixed"] = bool(a[0]["rounds"] == b[0]["rounds"] and torch.equal(a[1], b[1])
                                             and torch.equal(a[2], b[2]))
@@ -682,11 +675,14 @@ def separate_builds_concurrent(pts, Ks, seeds, outs, rounds, stride=4, dev=None,
                 res.append((i, h.build(pts[i], seeds[i], idx, key, flag)["rounds"]))
             return res
 
-        t0 = time.perf_counter()
-        with cf.ThreadPoolExecutor(streams) as ex:
-            done = [r for rr in ex.map(drive, range(streams)) for r in rr]
-        torch.cuda.synchronize()
-        total += time.perf_counter() - t0
+        best = float("inf")
+        for _ in range(2):  # the better of two timings of the wave: the baseline's most favourable
+            t0 = time.perf_counter()
+            with cf.ThreadPoolExecutor(streams) as ex:
+                done = [r for rr in ex.map(drive, range(streams)) for r in rr]
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        total += best
         rmap = dict(done)
         for i, h, idx, key, flag in hs:
             same += int(rmap[i] == rounds[i] and torch.equal(idx, outs[i][0]) and torch.equal(key, outs[i][1]))
@@ -694,7 +690,7 @@ def separate_builds_concurrent(pts, Ks, seeds, outs, rounds, stride=4, dev=None,
     return {"est_s": total * len(pts) / len(sel), "identical": f"{same}/{len(sel)}",
             "how": (f"{len(sel)} instances (every {stride}th), each its own knnd_build on one of {streams} "
                     f"streams driven by {streams} host threads, handles made outside the timing; wall clock "
-                    f"scaled to {len(pts)}")}
+                    f"of each wave of {wave} the better of two runs, summed and scaled to {len(pts)}")}
 
 
 def pad_m(m):

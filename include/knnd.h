@@ -103,7 +103,18 @@ typedef struct {
     int32_t merge_keep;           /* candidates each lane of the merge's fast path keeps (4 or 8; K <= 32) */
     int32_t join_blocks;          /* resident 128-thread blocks per SM of the FP32 TMA join (1..8; at most
                                      what fits) */
+    int32_t join_form;            /* KNND_JOIN_TMA or KNND_JOIN_PLAIN: how the FP32 filter gathers its rows
+                                     (0: the tuning table's, TMA only from n >= 65536 on); the TMA form
+                                     needs up to 32 padded coordinates, K <= 32, no incremental proposals
+                                     and not the inner product, else plain loads are used */
 } knnd_params;
+
+/* The join kernel a build ran (knnd_build_info.join_kernel); the first two are
+ * also the values of knnd_params.join_form. */
+#define KNND_JOIN_TMA 1   /* FP32 filter, rows and columns gathered into shared memory by TMA */
+#define KNND_JOIN_PLAIN 2 /* FP32 filter, rows gathered by plain loads */
+#define KNND_JOIN_FP64 3  /* every pair in FP64 (precision FP64) */
+#define KNND_JOIN_TC 4    /* BF16 hi/lo tiles on the tcgen05 tensor cores (precision MIXED_BF16X3) */
 
 /* The round loop of knnd_build.  Both give the same graph and report. */
 #define KNND_LOOP_AUTO 0  /* GRAPH, or HOST when timing = 1 */
@@ -143,6 +154,8 @@ typedef struct {
     int64_t merge_fallbacks;                 /* rows the merge finished on its serial path */
     int64_t join_survivors;                  /* candidates the join passed to the merge, all rounds */
     int64_t bound_audited;                   /* debug audit: pairs whose low-precision dot was checked */
+    int32_t join_kernel;                     /* KNND_JOIN_*: the join the rounds ran */
+    int32_t reserved;
 } knnd_build_info;
 
 /* Phases of the descent, for the per-phase timing of knnd_stats. */

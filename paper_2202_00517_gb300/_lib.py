@@ -40,6 +40,10 @@ KNND_CMP_INNER = 3
 KNND_LOOP_AUTO = 0
 KNND_LOOP_HOST = 1
 KNND_LOOP_GRAPH = 2
+KNND_JOIN_TMA = 1
+KNND_JOIN_PLAIN = 2
+KNND_JOIN_FP64 = 3
+KNND_JOIN_TC = 4
 
 EXPORTS = [
     "knnd_create", "knnd_destroy", "knnd_set_stream", "knnd_prepare", "knnd_init_graph", "knnd_round",
@@ -57,7 +61,7 @@ class knnd_params(ctypes.Structure):
                 ("stop_on_zero_updates", ctypes.c_int32), ("debug", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("incremental", ctypes.c_int32), ("stop_delta", ctypes.c_float),
                 ("comparator", ctypes.c_int32), ("loop", ctypes.c_int32), ("split_den", ctypes.c_int32),
-                ("merge_keep", ctypes.c_int32), ("join_blocks", ctypes.c_int32)]
+                ("merge_keep", ctypes.c_int32), ("join_blocks", ctypes.c_int32), ("join_form", ctypes.c_int32)]
 
 
 class knnd_build_info(ctypes.Structure):
@@ -67,7 +71,7 @@ class knnd_build_info(ctypes.Structure):
                 ("proposals", ctypes.c_int64), ("init_pairs", ctypes.c_int64),
                 ("rescored", ctypes.c_int64), ("bound_violations", ctypes.c_int64),
                 ("merge_fallbacks", ctypes.c_int64), ("join_survivors", ctypes.c_int64),
-                ("bound_audited", ctypes.c_int64)]
+                ("bound_audited", ctypes.c_int64), ("join_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 KNND_NUM_PHASES = 6

@@ -20,6 +20,9 @@ _PREC = {"fp64": _lib.KNND_PREC_FP64, "mixed": _lib.KNND_PREC_MIXED_FP32,
 _CMP = {"kl": _lib.KNND_CMP_KL, "kl_reverse": _lib.KNND_CMP_KL_REVERSE, "sqeuclidean": _lib.KNND_CMP_SQEUCLIDEAN,
         "inner": _lib.KNND_CMP_INNER}
 _LOOP = {"auto": _lib.KNND_LOOP_AUTO, "host": _lib.KNND_LOOP_HOST, "graph": _lib.KNND_LOOP_GRAPH}
+_JOIN = {"auto": 0, "tma": _lib.KNND_JOIN_TMA, "plain": _lib.KNND_JOIN_PLAIN}
+_JOIN_NAMES = {_lib.KNND_JOIN_TMA: "tma", _lib.KNND_JOIN_PLAIN: "plain", _lib.KNND_JOIN_FP64: "fp64",
+               _lib.KNND_JOIN_TC: "tc"}
 _DTYPE = {"f32": _lib.KNND_F32, "f64": _lib.KNND_F64, torch.float32: _lib.KNND_F32,
           torch.float64: _lib.KNND_F64}
 
@@ -48,7 +51,7 @@ def _info_dict(info: _lib.knnd_build_info) -> dict:
             "proposals": info.proposals, "init_pairs": info.init_pairs,
             "rescored": info.rescored, "bound_violations": info.bound_violations,
             "merge_fallbacks": info.merge_fallbacks, "join_survivors": info.join_survivors,
-            "bound_audited": info.bound_audited}
+            "bound_audited": info.bound_audited, "join_kernel": _JOIN_NAMES.get(info.join_kernel, "none")}
 
 
 class Handle:
@@ -57,14 +60,15 @@ class Handle:
     def __init__(self, n: int, m: int, K: int, dtype="f32", precision="mixed", fcc_samples: int = 10000,
                  max_rounds: int = 64, stop_on_zero_updates: bool = True, debug: bool = False,
                  timing: bool = False, incremental: bool = False, stop_delta: float = 0.0, comparator: str = "kl",
-                 loop: str = "auto", stream=None, split_den: int = 0, merge_keep: int = 0, join_blocks: int = 0):
+                 loop: str = "auto", stream=None, split_den: int = 0, merge_keep: int = 0, join_blocks: int = 0,
+                 join_form: str = "auto"):
         lib = _lib.load()
         self.n, self.m, self.K = n, m, K
         self.dtype = _DTYPE[dtype]
         self.torch_dtype = torch.float32 if self.dtype == _lib.KNND_F32 else torch.float64
         prm = _lib.knnd_params(fcc_samples, max_rounds, int(stop_on_zero_updates), int(debug), int(timing),
                                int(incremental), float(stop_delta), _CMP[comparator], _LOOP[loop], int(split_den),
-                               int(merge_keep), int(join_blocks))
+                               int(merge_keep), int(join_blocks), _JOIN[join_form])
         h = ctypes.c_void_p()
         check(lib.knnd_create(ctypes.byref(h), n, m, K, self.dtype, _PREC[precision], ctypes.byref(prm),
                               _stream_ptr(stream)), "knnd_create")
@@ -181,7 +185,8 @@ def build(points, K: int, seed: int = 0, precision: str = "mixed", **kw) -> dict
 def build_batched(points_list, Ks, seeds, precision: str = "mixed", fcc_samples: int = 10000,
                   max_rounds: int = 64, stop_on_zero_updates: bool = True, workspace_limit: int = 0,
                   incremental: bool = False, stop_delta: float = 0.0, comparator: str = "kl", stream=None,
-                  outputs=None, split_den: int = 0, merge_keep: int = 0, join_blocks: int = 0):
+                  outputs=None, split_den: int = 0, merge_keep: int = 0, join_blocks: int = 0,
+                  join_form: str = "auto"):
     """Batched form: build many independent instances together.
 
     points_list: CUDA tensors (n_i x m_i, one dtype for all); Ks, seeds: per instance.
@@ -210,7 +215,7 @@ def build_batched(points_list, Ks, seeds, precision: str = "mixed", fcc_samples:
         arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, K, sd, idx.data_ptr(), key.data_ptr())
     prm = _lib.knnd_params(fcc_samples, max_rounds, int(stop_on_zero_updates), 0, 0, int(incremental),
                            float(stop_delta), _CMP[comparator], _lib.KNND_LOOP_AUTO, int(split_den), int(merge_keep),
-                           int(join_blocks))
+                           int(join_blocks), _JOIN[join_form])
     infos = (_lib.knnd_build_info * count)()
     check(lib.knnd_build_batched(count, ctypes.cast(arr, ctypes.c_void_p), dtype, _PREC[precision],
                                  ctypes.byref(prm), workspace_limit, ctypes.cast(infos, ctypes.c_void_p),

@@ -4,7 +4,8 @@ The choices change the speed of a build, never its result (the tests build the
 same graphs under every choice):
   split_den   round 1 first runs the hubs [0, n / split_den), 1 = one phase;
   merge_keep  candidates each lane of the merge's fast path keeps (4 or 8);
-  join_blocks resident blocks per SM of the FP32 TMA join (0 = as many as fit).
+  join_blocks resident blocks per SM of the FP32 TMA join (0 = as many as fit);
+  join_tma    1: the FP32 join gathers by TMA where that form applies, 0: plain loads.
 
 Classes: the (m, K) classes of the 4,096-instance mix (m in {6, 11, 21},
 K in {8, 16, 32}), the n = 1e6, d = 20, K = 20 shape and the n = 4e6, d = 64,
@@ -41,7 +42,7 @@ OUT = os.path.join(HERE, "csrc", "tune_table.h")
 SPLITS = (1, 4, 8, 16)
 KEEPS = (4, 8)
 BLOCKS = (0, 4, 3)
-DEFAULT = (8, 4, 0)
+DEFAULT = (8, 4, 0, 1)
 MARGIN = 0.01
 
 
@@ -74,8 +75,9 @@ def time_batched(pts, Ks, seeds, choice, reps=2):
         key = torch.empty((n, k), dtype=torch.float64, device=p.device)
         outs.append((idx, key))
         arr[i] = _lib.knnd_instance(p.data_ptr(), p.stride(0), n, m, k, seeds[i], idx.data_ptr(), key.data_ptr())
-    s, keep, blocks = choice
-    prm = _lib.knnd_params(10000, 64, 1, 0, 0, 0, 0.0, 0, 0, s, keep, blocks)
+    s, keep, blocks, tma = choice
+    prm = _lib.knnd_params(10000, 64, 1, 0, 0, 0, 0.0, 0, 0, s, keep, blocks,
+                           _lib.KNND_JOIN_TMA if tma else _lib.KNND_JOIN_PLAIN)
     b = ctypes.c_void_p()
     stream = torch.cuda.current_stream()
     st = ctypes.c_void_p(stream.cuda_stream)
@@ -101,9 +103,10 @@ def time_single(p, K, seed, choice, reps=2):
     import torch
 
     import paper_2202_00517_gb300 as knnd
-    s, keep, blocks = choice
+    s, keep, blocks, tma = choice
     n, m = p.shape
-    h = knnd.Handle(n, m, K, dtype="f32", precision="mixed", split_den=s, merge_keep=keep, join_blocks=blocks)
+    h = knnd.Handle(n, m, K, dtype="f32", precision="mixed", split_den=s, merge_keep=keep, join_blocks=blocks,
+                    join_form="tma" if tma else "plain")
     idx, key, flag = h.new_graph(p.device)
     stream = torch.cuda.current_stream()
     try:
@@ -123,10 +126,15 @@ def time_single(p, K, seed, choice, reps=2):
 
 
 def choices_for(mp: int, K: int, quick: bool):
-    blocks = BLOCKS if (mp <= 32 and K <= 32) else (0,)
+    tma_ok = mp <= 32 and K <= 32
     if quick:
-        return [DEFAULT, (4, 4, 0), (8, 8, 0)]
-    return list(itertools.product(SPLITS, KEEPS, blocks))
+        return [DEFAULT, (4, 4, 0, 1), (8, 8, 0, 1), (8, 4, 0, 0)]
+    out = []
+    for s, keep in itertools.product(SPLITS, KEEPS):
+        out += [(s, keep, b, 1) for b in (BLOCKS if tma_ok else (0,))]
+        if tma_ok:
+            out.append((s, keep, 0, 0))
+    return out
 
 
 def main(argv=None):
@@ -166,20 +174,21 @@ def write_table(path, results, device):
         "//   split_den:   round 1 runs the hubs [0, n / split_den) first (1: one phase)",
         "//   merge_keep:  candidates each lane of the merge's fast path keeps (4 or 8)",
         "//   join_blocks: resident blocks per SM of the FP32 TMA join (0: as many as fit)",
+        "//   join_tma:    1: the FP32 join gathers by TMA where that form applies; 0: plain loads",
         "#pragma once",
         "",
         "namespace knnd {",
         "",
         "struct TuneEntry {",
         "    int MP, K_lo, K_hi;",
-        "    int split_den, merge_keep, join_blocks;",
+        "    int split_den, merge_keep, join_blocks, join_tma;",
         "};",
         "",
-        f"constexpr TuneEntry kTuneDefault = {{0, 0, 0, {DEFAULT[0]}, {DEFAULT[1]}, {DEFAULT[2]}}};",
+        f"constexpr TuneEntry kTuneDefault = {{0, 0, 0, {DEFAULT[0]}, {DEFAULT[1]}, {DEFAULT[2]}, {DEFAULT[3]}}};",
         "",
         f"// Measured on {device}, {datetime.date.today().isoformat()}, by",
         "//   python -m paper_2202_00517_gb300.autotune",
-        "// Per class: the workload, the fastest choice (split_den, merge_keep, join_blocks)",
+        "// Per class: the workload, the fastest choice (split_den, merge_keep, join_blocks, join_tma)",
         "// with its time, and the default's time (CUDA events, best of two runs); the",
         f"// entry holds the fastest choice only when it beats the default by more than {MARGIN:.0%}.",
         "constexpr TuneEntry kTuneTable[] = {",
@@ -191,7 +200,7 @@ def write_table(path, results, device):
         pick = best if (d is None or t < d * (1.0 - MARGIN)) else DEFAULT
         lines.append(f"    // m = {m}, K = {K}: {workload}; fastest {best} {t:.2f} ms, default "
                      f"{'%.2f ms' % d if d is not None else 'not timed'}")
-        lines.append(f"    {{{mp}, {lo}, {hi}, {pick[0]}, {pick[1]}, {pick[2]}}},")
+        lines.append(f"    {{{mp}, {lo}, {hi}, {pick[0]}, {pick[1]}, {pick[2]}, {pick[3]}}},")
     lines += ["};", "", "}  // namespace knnd", ""]
     with open(path, "w") as fh:
         fh.write("\n".join(lines))

@@ -372,6 +372,7 @@ knnd_status graph_rounds(knnd_handle *h, uint64_t seed, int32_t *idx, double *ke
     info->merge_fallbacks = st.sums[2];
     info->join_survivors = st.sums[3];
     info->bound_audited = st.sums[4];
+    info->join_kernel = h->join_kernel;
     info->proposals = (int64_t)R * h->n * (int64_t)h->K * (2 * (int64_t)h->K + 1);
     h->launches += 1 + h->loop_first_launches + (int64_t)(R - 1) * h->loop_round_launches;
     h->rounds_run += R;
@@ -402,6 +403,7 @@ knnd_params default_params()
     p.split_den = 0;
     p.merge_keep = 0;
     p.join_blocks = 0;
+    p.join_form = 0;
     return p;
 }
 
@@ -424,6 +426,7 @@ void configure(knnd_handle *h, int64_t n, int32_t m, int32_t K)
     h->split_den = h->prm.split_den > 0 ? h->prm.split_den : t.split_den;
     h->merge_keep = h->prm.merge_keep > 0 ? h->prm.merge_keep : t.merge_keep;
     h->join_blocks = h->prm.join_blocks > 0 ? h->prm.join_blocks : t.join_blocks;
+    h->join_form = h->prm.join_form > 0 ? h->prm.join_form : (t.join_tma ? KNND_JOIN_TMA : KNND_JOIN_PLAIN);
 }
 
 knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd_precision precision,
@@ -443,7 +446,6 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
         return KNND_ECUDA;
     }
     if (const char *f = std::getenv("KNND_TEST_FAIL_ALLOC")) h->fail_alloc_at = std::atoi(f);
-    if (const char *j = std::getenv("KNND_JOIN")) h->join_lsu = std::strcmp(j, "lsu") == 0 ? 1 : 0;
     const int64_t n = c.n;
     knnd_status s = KNND_OK;
     const int64_t ntiles = (n + 2047) / 2048;
@@ -701,6 +703,7 @@ knnd_status knnd_build(knnd_handle *h, const void *points, int64_t ld, uint64_t 
         info->merge_fallbacks += hst[kCntFallback];
         info->join_survivors += hst[kCntSurvivors];
         info->bound_audited += hst[kCntAudited];
+        info->join_kernel = h->join_kernel;
         info->proposals += per_round;
         info->rounds = r;
         if (info->fcc_hits[r] <= info->fcc_hits[r - 1]) {

@@ -155,6 +155,7 @@ struct SubBatch {
     cudaGraphExec_t exec;
     int64_t launches_outer;  // kernels outside the loop body (set-up, round 1, export)
     int64_t launches_round;  // kernels of one round of the body
+    int32_t join_kernel;     // KNND_JOIN_*: the join its rounds run
 };
 
 // A workspace and its stream: runs its sub-batches one after the other.
@@ -383,6 +384,7 @@ knnd_status capture_sub(knnd_batch *b, SubBatch &sb)
         e = end_capture(np.conditional.phGraph_out[0], false);
     }
     const int64_t l2 = h->launches;
+    sb.join_kernel = h->join_kernel;
     // after the loop: every instance's graph to its own arrays
     if (!e && !s) e = cudaStreamBeginCaptureToGraph(st, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
     if (!e && !s) {
@@ -607,6 +609,7 @@ knnd_status knnd_batch_run(knnd_batch *b, knnd_build_info *info)
             o.proposals = (int64_t)o.rounds * in.n * in.K * (2 * (int64_t)in.K + 1);
             o.rescored = resc[j];
             o.merge_fallbacks = fb[j];
+            o.join_kernel = sb.join_kernel;
         }
     }
     return KNND_OK;

@@ -757,13 +757,17 @@ static cudaError_t run_join_cpl(knnd_handle *h, const JoinArgs &a)
 
 cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase, int split_den)
 {
-    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && h->prm.comparator == KNND_CMP_KL)
+    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && h->prm.comparator == KNND_CMP_KL) {
+        h->join_kernel = KNND_JOIN_TC;
         return launch_join_tc(h, idx, h_lo, h_hi, phase, split_den);
-    if (!h->join_lsu && tma_join_supported(h)) {
+    }
+    if (h->join_form == KNND_JOIN_TMA && tma_join_supported(h)) {
         cudaMemsetAsync(h->bcnt, 0, sizeof(int32_t) * h->n, h->stream);
         h->launches += 1;
+        h->join_kernel = KNND_JOIN_TMA;
         return launch_join_tma(h, idx, h_lo, h_hi, phase, split_den);
     }
+    h->join_kernel = h->prec == KNND_PREC_FP64 ? KNND_JOIN_FP64 : KNND_JOIN_PLAIN;
     JoinArgs a;
     a.n = h->n;
     a.h_lo = h_lo;

@@ -185,9 +185,10 @@ struct knnd_handle {
     int device;
     int num_sms;
     int fail_alloc_at;  // > 0: the fail_alloc_at-th workspace allocation fails (KNND_TEST_FAIL_ALLOC)
-    int join_lsu;       // 1: the mixed join gathers with plain loads even where the TMA form applies (KNND_JOIN=lsu)
     // execution choices for the current shape (params, else the tuning table)
     int split_den, merge_keep, join_blocks;
+    int join_form;    // KNND_JOIN_TMA or KNND_JOIN_PLAIN (params, else the tuning table)
+    int join_kernel;  // KNND_JOIN_*: the join the last launch_join ran
     int allocs;
     bool prepared;
 
@@ -338,7 +339,7 @@ inline TuneEntry tune_lookup(int MP, int K)
 inline bool tuning_valid(const knnd_params &p)
 {
     return p.split_den >= 0 && p.split_den <= 64 && (p.merge_keep == 0 || p.merge_keep == 4 || p.merge_keep == 8) &&
-           p.join_blocks >= 0 && p.join_blocks <= 8;
+           p.join_blocks >= 0 && p.join_blocks <= 8 && p.join_form >= 0 && p.join_form <= KNND_JOIN_PLAIN;
 }
 
 inline int pad_coords(int m) {

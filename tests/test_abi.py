@@ -42,10 +42,10 @@ def test_version_and_status_strings(lib):
 
 
 def test_struct_layouts():
-    # host structs of the header: eleven int32 params and a float; build info 8 + 64*8 + 65*8 + 7*8 bytes;
-    # stats 3 int64 + 6 int64 + 6 double
-    assert ctypes.sizeof(_lib.knnd_params) == 48
-    assert ctypes.sizeof(_lib.knnd_build_info) == 8 + 64 * 8 + 65 * 8 + 7 * 8
+    # host structs of the header: twelve int32 params and a float; build info 8 + 64*8 + 65*8 + 7*8 + 8
+    # bytes; stats 3 int64 + 6 int64 + 6 double
+    assert ctypes.sizeof(_lib.knnd_params) == 52
+    assert ctypes.sizeof(_lib.knnd_build_info) == 8 + 64 * 8 + 65 * 8 + 7 * 8 + 8
     assert ctypes.sizeof(_lib.knnd_stats) == 3 * 8 + 6 * 8 + 6 * 8
 
 
@@ -78,7 +78,8 @@ def test_create_rejects_bad_params(lib):
                 _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, 65),     # split share out of range
                 _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, -1),
                 _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, 0, 5),   # merge keeps 4 or 8
-                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, 0, 0, 9)):  # join blocks out of range
+                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, 0, 0, 9),   # join blocks out of range
+                _lib.knnd_params(100, 10, 1, 0, 0, 0, 0.0, 0, 0, 0, 0, 0, 3)):  # no such join form
         assert lib.knnd_create(ctypes.byref(h), 1000, 6, 10, 0, 1, ctypes.byref(prm), None) == _lib.KNND_EINVAL
     assert lib.knnd_create(None, 1000, 6, 10, 0, 1, None, None) == _lib.KNND_EINVAL
 

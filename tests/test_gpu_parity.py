@@ -24,7 +24,15 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ("fp64", "mixed", "bf16x3")
+# "mixed_tma": the mixed form with the TMA-gathered join forced (by default it runs
+# from n = 65,536 on; these shapes are smaller)
+PRECS = ("fp64", "mixed", "mixed_tma", "bf16x3")
+
+
+def _handle(knnd, *args, precision="mixed", **kw):
+    if precision == "mixed_tma":
+        precision, kw["join_form"] = "mixed", "tma"
+    return knnd.Handle(*args, precision=precision, **kw)
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +49,7 @@ def _dev(a):
 def _lockstep(knnd, pts, K, seed, prec, rounds, dtype="f64", S=2000, incremental=True, comparator="kl"):
     n, m = pts.shape
     p = _dev(pts)
-    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, fcc_samples=S, incremental=incremental,
+    h = _handle(knnd, n, m, K, dtype=dtype, precision=prec, fcc_samples=S, incremental=incremental,
                     comparator=comparator)
     pts64 = pts.astype(np.float64)
     gi, gk, _ = h.init_graph(p, seed)
@@ -83,7 +91,7 @@ def test_config1_build_equals_oracle(knnd, prec):
     n, m, K, seed = 2000, 6, 10, 0
     pts = dirichlet_points(n, m, seed, np.float64)
     ref = oracle.build(pts, K, seed)
-    h = knnd.Handle(n, m, K, dtype="f64", precision=prec)
+    h = _handle(knnd, n, m, K, dtype="f64", precision=prec)
     out = h.build(_dev(pts), seed)
     assert out["rounds"] == ref["rounds"]
     assert out["updates"] == list(ref["updates"])
@@ -139,11 +147,11 @@ def test_skewed_points_lockstep(knnd, prec, dtype, power):
     ties = _lockstep(knnd, pts, K, seed, prec, rounds=3, dtype=dtype, S=500)
     assert ties <= max(2, n // 500)
     p = _dev(pts)
-    h = knnd.Handle(n, m, K, dtype=dtype, precision=prec, debug=True)
+    h = _handle(knnd, n, m, K, dtype=dtype, precision=prec, debug=True)
     out = h.build(p, seed)
     h.close()
     assert out["bound_violations"] == 0
-    ref = knnd.Handle(n, m, K, dtype=dtype, precision="fp64")
+    ref = _handle(knnd, n, m, K, dtype=dtype, precision="fp64")
     r = ref.build(p, seed)
     ref.close()
     assert torch.equal(out["idx"], r["idx"]) and torch.equal(out["key"], r["key"])
@@ -160,7 +168,7 @@ def test_duplicated_points_exact_ties(knnd, prec):
     # Free-running, each side keys every copy identically: ties go by index and
     # the graphs must be identical.
     ref = oracle.build(pts, 8, 11, S=500)
-    h = knnd.Handle(len(pts), 5, 8, dtype="f64", precision=prec, fcc_samples=500)
+    h = _handle(knnd, len(pts), 5, 8, dtype="f64", precision=prec, fcc_samples=500)
     out = h.build(_dev(pts), 11)
     h.close()
     assert out["rounds"] == ref["rounds"] and out["updates"] == list(ref["updates"])
@@ -183,7 +191,7 @@ def test_incremental_proposals_same_graph(knnd, n, m, K):
     for prec in PRECS:
         res = {}
         for inc in (False, True):
-            h = knnd.Handle(n, m, K, dtype="f32", precision=prec, incremental=inc)
+            h = _handle(knnd, n, m, K, dtype="f32", precision=prec, incremental=inc)
             res[inc] = h.build(pts, seed)
             h.close()
         a, b = res[False], res[True]
@@ -192,17 +200,17 @@ def test_incremental_proposals_same_graph(knnd, n, m, K):
         assert b["join_survivors"] < a["join_survivors"], prec
 
 
-@pytest.mark.parametrize("n,m,K", [(200_000, 21, 20), (60_000, 65, 32)])
+@pytest.mark.parametrize("n,m,K", [(200_000, 21, 20), (60_000, 65, 32), (50_000, 11, 32)])
 def test_mixed_forms_equal_fp64_bitwise(knnd, n, m, K):
     seed = 1
     pts = _dev(dirichlet_points(n, m, seed, np.float32))
     res = {}
     for prec in PRECS:
-        h = knnd.Handle(n, m, K, dtype="f32", precision=prec)
+        h = _handle(knnd, n, m, K, dtype="f32", precision=prec)
         res[prec] = h.build(pts, seed)
         h.close()
     a = res["fp64"]
-    for prec in ("mixed", "bf16x3"):
+    for prec in ("mixed", "mixed_tma", "bf16x3"):
         b = res[prec]
         assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"], prec
         assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["key"], b["key"]), prec
@@ -210,7 +218,7 @@ def test_mixed_forms_equal_fp64_bitwise(knnd, n, m, K):
     check_invariants(a["idx"].cpu().numpy(), a["key"].cpu().numpy())
 
 
-@pytest.mark.parametrize("prec", ["mixed", "bf16x3"])
+@pytest.mark.parametrize("prec", ["mixed", "mixed_tma", "bf16x3"])
 @pytest.mark.parametrize("m,K", [(21, 20), (65, 32), (6, 10)])
 def test_error_bound_audit(knnd, prec, m, K):
     # debug mode checks every low-precision dot the tensor-core join and the
@@ -218,13 +226,14 @@ def test_error_bound_audit(knnd, prec, m, K):
     # against the FP64 dot: none may exceed the bound the filter relies on
     n = 6000
     pts = _dev(dirichlet_points(n, m, 17, np.float32))
-    h = knnd.Handle(n, m, K, dtype="f32", precision=prec, debug=True)
+    h = _handle(knnd, n, m, K, dtype="f32", precision=prec, debug=True)
     out = h.build(pts, 17)
     h.close()
     assert out["bound_violations"] == 0
-    if prec == "bf16x3" or (m <= 32 and K <= 32):
+    if prec == "bf16x3" or (prec == "mixed_tma" and m <= 32 and K <= 32):
         assert out["bound_audited"] > n * K
-    ref = knnd.Handle(n, m, K, dtype="f32", precision="fp64")
+        assert out["join_kernel"] == ("tc" if prec == "bf16x3" else "tma")
+    ref = _handle(knnd, n, m, K, dtype="f32", precision="fp64")
     r = ref.build(pts, 17)
     ref.close()
     assert torch.equal(out["idx"], r["idx"]) and torch.equal(out["key"], r["key"])
@@ -233,7 +242,7 @@ def test_error_bound_audit(knnd, prec, m, K):
 def test_domain_errors_and_recovery(knnd):
     n, m, K = 500, 6, 8
     pts = dirichlet_points(n, m, 3, np.float64)
-    h = knnd.Handle(n, m, K, dtype="f64", precision="mixed")
+    h = _handle(knnd, n, m, K, dtype="f64", precision="mixed")
     for bad in (0.0, -0.5, np.nan, np.inf):
         q = pts.copy()
         q[123, 4] = bad
@@ -251,7 +260,7 @@ def test_out_of_range_indices_are_reported(knnd):
     # recorded, and knnd_sync reports EINVAL.
     n, m, K = 400, 4, 6
     pts = dirichlet_points(n, m, 5, np.float64)
-    h = knnd.Handle(n, m, K, dtype="f64", precision="mixed")
+    h = _handle(knnd, n, m, K, dtype="f64", precision="mixed")
     idx, key, flag = h.init_graph(_dev(pts), 5)
     h.sync()
     idx[7, 2] = n + 5
@@ -271,7 +280,7 @@ def test_delta_proportion_stop_matches_oracle(knnd, prec):
     ref_full = oracle.build(pts, K, seed, S=S)
     delta = (ref_full["updates"][2] + 0.5) / (n * K)
     ref = oracle.build(pts, K, seed, S=S, stop_delta=delta)
-    h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, stop_delta=delta)
+    h = _handle(knnd, n, m, K, dtype="f64", precision=prec, fcc_samples=S, stop_delta=delta)
     out = h.build(_dev(pts), seed)
     h.close()
     assert out["rounds"] == ref["rounds"] == 3
@@ -295,7 +304,7 @@ def test_reverse_direction_build(knnd):
     ref = oracle.build(pts, K, seed, S=S, comparator="kl_reverse")
     outs = {}
     for prec in PRECS:
-        h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="kl_reverse")
+        h = _handle(knnd, n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="kl_reverse")
         outs[prec] = h.build(_dev(pts), seed)
         h.close()
     for prec, out in outs.items():
@@ -326,7 +335,7 @@ def test_sqeuclidean_build(knnd):
     ref = oracle.build(pts, K, seed, S=S, comparator="sqeuclidean")
     outs = {}
     for prec in PRECS:
-        h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="sqeuclidean")
+        h = _handle(knnd, n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="sqeuclidean")
         outs[prec] = h.build(_dev(pts), seed)
         h.close()
     for prec, out in outs.items():
@@ -344,7 +353,7 @@ def test_sqeuclidean_build(knnd):
 def test_sqeuclidean_domain(knnd):
     n, m, K = 300, 4, 6
     pts = _gauss(n, m, 5)
-    h = knnd.Handle(n, m, K, dtype="f64", precision="mixed", comparator="sqeuclidean")
+    h = _handle(knnd, n, m, K, dtype="f64", precision="mixed", comparator="sqeuclidean")
     h.build(_dev(pts), 5)  # negative and zero coordinates are fine here
     bad = pts.copy()
     bad[7, 1] = np.nan
@@ -352,7 +361,7 @@ def test_sqeuclidean_domain(knnd):
         h.build(_dev(bad), 5)
     assert e.value.status == knnd.api._lib.KNND_EDOMAIN
     h.close()
-    hk = knnd.Handle(n, m, K, dtype="f64", precision="mixed")  # KL needs coordinates > 0
+    hk = _handle(knnd, n, m, K, dtype="f64", precision="mixed")  # KL needs coordinates > 0
     with pytest.raises(knnd.api._lib.KnndError) as e:
         hk.build(_dev(pts), 5)
     assert e.value.status == knnd.api._lib.KNND_EDOMAIN
@@ -375,7 +384,7 @@ def test_inner_product_build(knnd):
     ref = oracle.build(pts, K, seed, S=S, comparator="inner")
     outs = {}
     for prec in PRECS:
-        h = knnd.Handle(n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="inner")
+        h = _handle(knnd, n, m, K, dtype="f64", precision=prec, fcc_samples=S, comparator="inner")
         outs[prec] = h.build(_dev(pts), seed)
         h.close()
     for prec, out in outs.items():
@@ -395,33 +404,36 @@ def test_bounded_wait_timeout_is_reported(knnd):
     # and the GPU context stays usable (no fault is involved)
     n, m, K, seed = 3000, 21, 20, 3
     pts = _dev(dirichlet_points(n, m, seed, np.float32))
-    h = knnd.Handle(n, m, K, dtype="f32", precision="bf16x3", debug=2)
+    h = _handle(knnd, n, m, K, dtype="f32", precision="bf16x3", debug=2)
     with pytest.raises(knnd.api._lib.KnndError) as e:
         h.build(pts, seed)
     assert e.value.status == knnd.api._lib.KNND_ETIMEOUT
     h.close()
-    h = knnd.Handle(n, m, K, dtype="f32", precision="bf16x3")
+    h = _handle(knnd, n, m, K, dtype="f32", precision="bf16x3")
     out = h.build(pts, seed)
     h.close()
-    ref = knnd.Handle(n, m, K, dtype="f32", precision="fp64")
+    ref = _handle(knnd, n, m, K, dtype="f32", precision="fp64")
     r = ref.build(pts, seed)
     ref.close()
     assert torch.equal(out["idx"], r["idx"])
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-@pytest.mark.parametrize("n,m,K", [(20000, 21, 20), (6000, 11, 32), (8000, 6, 8)])
-@pytest.mark.parametrize("choice", [(1, 4, 0), (4, 8, 3), (16, 8, 1), (2, 4, 5)])
+@pytest.mark.parametrize("n,m,K", [(70000, 21, 20), (6000, 11, 32), (66000, 6, 8)])
+@pytest.mark.parametrize("choice", [(1, 4, 0, "tma"), (4, 8, 3, "tma"), (16, 8, 1, "plain"), (2, 4, 5, "tma"),
+                                    (8, 4, 0, "plain")])
 def test_tuning_choices_same_graph(knnd, prec, n, m, K, choice):
     # the execution choices of the tuning table (round 1's split share, the
-    # merge's per-lane keep, the TMA join's blocks per SM) change the speed only
+    # merge's per-lane keep, the TMA join's blocks per SM, the join's gathers)
+    # change the speed only
     seed = 5
     pts = _dev(dirichlet_points(n, m, seed, np.float32))
-    ref = knnd.Handle(n, m, K, dtype="f32", precision=prec)
+    ref = _handle(knnd, n, m, K, dtype="f32", precision=prec)
     a = ref.build(pts, seed)
     ref.close()
-    s, keep, blocks = choice
-    h = knnd.Handle(n, m, K, dtype="f32", precision=prec, split_den=s, merge_keep=keep, join_blocks=blocks)
+    s, keep, blocks, form = choice
+    h = _handle(knnd, n, m, K, dtype="f32", precision=prec, split_den=s, merge_keep=keep, join_blocks=blocks,
+                    join_form=form)
     b = h.build(pts, seed)
     h.close()
     assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"]
@@ -434,7 +446,7 @@ def test_tuning_choices_batched_same_graphs(knnd):
     Ks = [K for _, _, K in shapes]
     seeds = [900 + i for i in range(len(shapes))]
     a = knnd.build_batched(pts, Ks, seeds)
-    b = knnd.build_batched(pts, Ks, seeds, split_den=1, merge_keep=8, join_blocks=2)
+    b = knnd.build_batched(pts, Ks, seeds, split_den=1, merge_keep=8, join_blocks=2, join_form="plain")
     for x, y in zip(a, b):
         assert x["rounds"] == y["rounds"] and x["updates"] == y["updates"]
         assert torch.equal(x["idx"], y["idx"]) and torch.equal(x["key"], y["key"])
