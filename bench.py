@@ -123,19 +123,29 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def code_sha256(path):
+    """sha256 of a C/CUDA source with its comments and all whitespace removed:
+    the same for two versions of a kernel that differ in comments or layout only.
+    (A string literal holding // or /* would be cut too; these sources have none
+    that matter to the code.)"""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return hashlib.sha256(re.sub(r"\s+", "", text).encode()).hexdigest()
+
+
 def join_traffic_per_launch(name, source="join.cu", profile_prefix="join_mixed"):
     """DRAM bytes per join launch from the committed ncu summary of the workload,
-    if it was taken on the current join source (sha256 recorded in the summary);
-    else None."""
+    if it was taken on the current join code (the summary records the source's
+    code_sha256); else None."""
     src = os.path.join(ROOT, "paper_2202_00517_gb300", "csrc", source)
     prof = os.path.join(ROOT, "profiles", f"{profile_prefix}_{name}.md")
     if not os.path.exists(prof):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     text = open(prof).read()
-    m_sha = re.search(re.escape(source) + r" sha256:\s*([0-9a-f]{64})", text)
+    m_sha = re.search(re.escape(source) + r" code sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", text)
-    if not (m_sha and m_b) or m_sha.group(1) != sha:
+    if not (m_sha and m_b) or m_sha.group(1) != code_sha256(src):
         return None
     return float(m_b.group(1))
 

@@ -45,12 +45,13 @@ void drop_loop_graph(knnd_handle *h);
 
 void free_all(knnd_handle *h)
 {
-    void *ptrs[] = {h->X64, h->L64, h->negH, h->nx, h->X32, h->L32, h->smax_bits, h->err, h->deg, h->slot,
-                    h->heavy_items, h->heavy_nitems,
-                    h->cof_off, h->cof, h->cof_new, h->flag_tmp, h->scan_tmp, h->tau, h->idxK, h->meta, h->Ex, h->bcnt, h->bkey,
-                    h->bent, h->fb_list, h->fb_T, h->join_queue, h->fb_count, h->cnt, h->pts_dev, h->idx_dev, h->key_dev, h->idxA, h->keyA,
-                    h->flagA,
-                    h->inst_of, h->inst_base, h->inst_n, h->inst_seed, h->inst_active, h->inst_cnt};
+    void *ptrs[] = {h->X64,      h->L64,        h->negH,    h->nx,         h->X32,      h->L32,
+                    h->smax_bits, h->err,        h->deg,     h->slot,       h->heavy_items, h->heavy_nitems,
+                    h->cof_off,  h->cof,        h->cof_new, h->flag_tmp,   h->scan_tmp, h->tau,
+                    h->idxK,     h->meta,       h->Ex,      h->bcnt,       h->bkey,     h->bent,
+                    h->fb_list,  h->fb_T,       h->join_queue, h->fb_count, h->cnt,     h->pts_dev,
+                    h->idx_dev,  h->key_dev,    h->idxA,    h->keyA,       h->flagA,    h->inst_of,
+                    h->inst_base, h->inst_n,    h->inst_seed, h->inst_active, h->inst_cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->cnt_host) cudaFreeHost(h->cnt_host);

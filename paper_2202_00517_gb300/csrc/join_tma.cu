@@ -6,10 +6,11 @@
 // rows of F(v), v itself; a pair is kept when its FP32 dot can still beat the
 // row's K-th entry.  What differs is how the tile reaches the FP32 pipe:
 //
-//  * a warp takes a hub's rows 32 at a time (an item); lane t owns row t of the
-//    item for the whole item: its coordinates sit in registers, so the dots of
-//    a row are finished in the lane that filters them and never pass through
-//    shared memory;
+//  * a warp takes a hub's rows 32 R at a time (an item; R = 1 is the one
+//    instantiated); lane t owns row t of the item (and t + 32 when R = 2) for
+//    the whole item: its coordinates sit in registers, so the dots of a row are
+//    finished in the lane that filters them and never pass through shared
+//    memory;
 //  * the 32 rows of an item and the K + 1 columns of a hub are gathered from
 //    the FP32 tables by cp.async.bulk.tensor ... tile::gather4 (four indexed
 //    rows of a two-dimensional tensor map per instruction, one row high), which
@@ -29,9 +30,10 @@
 // coordinates, run together by packed two-wide FP32 fmas (__ffma2_rn, one
 // instruction for both), then added: at most ceil(m/2) + 1 roundings on any
 // term, within the m + 6 that the filter's bound c_m = (m + 6) 2^-24 (1.01)
-// allows for (Higham, Sec. 3.1: the bound holds for any summation order).  debug = 1 audits every dot against FP64 for
-// the comparators whose bound is E_x itself.  Incremental proposals and the
-// inner product's heavy-hub pass stay with join.cu.
+// allows for (Higham, Sec. 3.1: the bound holds for any summation order).
+// debug = 1 audits every dot against FP64 for the comparators whose bound is
+// E_x itself.  Incremental proposals and the inner product's heavy-hub pass
+// stay with join.cu, and so do the shapes the tuning table gives to it.
 //
 // Every mbarrier wait is bounded (1 s of the global timer); on a timeout the
 // warp sets kErrTimeout, waits (bounded) for its copies in flight and stops.

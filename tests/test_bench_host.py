@@ -49,25 +49,27 @@ def test_pair_trend_falls_as_the_graph_clusters():
 
 def test_traffic_read_only_for_the_profiled_source(tmp_path, monkeypatch):
     # The roofline's DRAM traffic comes from a committed ncu summary, and only while
-    # the join source it was taken on is the current one (its sha256 recorded there).
-    import hashlib
+    # the join code it was taken on is the current one (its code hash recorded
+    # there): a comment or layout edit keeps it, a code edit drops it.
     src = tmp_path / "paper_2202_00517_gb300" / "csrc"
     src.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
-    (src / "join.cu").write_text("// join v1\n")
-    sha = hashlib.sha256(b"// join v1\n").hexdigest()
+    (src / "join.cu").write_text("// join v1\nint f() { return 1; }\n")
+    sha = bench.code_sha256(str(src / "join.cu"))
     (tmp_path / "profiles" / "join_mixed_w.md").write_text(
-        f"join.cu sha256: {sha}\n\ndram bytes per full-size launch: 9.5e+09\n")
+        f"join.cu code sha256: {sha}\n\ndram bytes per full-size launch: 9.5e+09\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.join_traffic_per_launch("w") == 9.5e9
     assert bench.join_traffic_per_launch("other") is None
-    (src / "join.cu").write_text("// join v2\n")
+    (src / "join.cu").write_text("/* join\n   v2 */\nint  f()\n{ return 1; }  // same code\n")
+    assert bench.join_traffic_per_launch("w") == 9.5e9
+    (src / "join.cu").write_text("// join v1\nint f() { return 2; }\n")
     assert bench.join_traffic_per_launch("w") is None
 
 
 def test_committed_profile_matches_the_join_source():
     # the benchmark workload's summary parses; its traffic is the join's, a few GB
-    t = bench.join_traffic_per_launch("n1e6_d20_K20")
+    t = bench.join_traffic_per_launch("n1e6_d20_K20", "join_tma.cu", "join_tma")
     assert t is None or 1e9 < t < 1e11
 
 
