@@ -442,10 +442,7 @@ __global__ void __launch_bounds__(128, R == 2 ? 3 : (MP <= 24 ? 5 : 4))
         int q[R];
         unsigned mk[R];  // bit j: column j passed
 #pragma unroll
-        for (int s = 0; s < R; ++s) {
-            q[s] = 0;
-            mk[s] = 0u;
-        }
+        for (int s = 0; s < R; ++s) mk[s] = 0u;
         for (int j0 = 0; j0 < K; j0 += 4) {
             // column j0 + k: chains over the even and the odd coordinates
             float2 e[R][4];
@@ -467,22 +464,34 @@ __global__ void __launch_bounds__(128, R == 2 ? 3 : (MP <= 24 ? 5 : 4))
                     }
                 }
             }
+            // the dot goes to the row's slot j whether it passes or not, and the pass
+            // bit needs one compare with the row's point (a column that is the row's
+            // own point is no pair); columns past K and columns without a point are
+            // masked out once, below
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int j = j0 + k;
+                const int j = j0 + k;   // j <= 31 (K <= 32)
                 const int cj = cid[j];  // j < K + 3 < 2 kSlot: inside the slot pair
                 const float h = COL ? hcol[j] : 0.f;
 #pragma unroll
                 for (int s = 0; s < R; ++s) {
                     const float d = __fadd_rn(e[s][k].x, e[s][k].y);
-                    const bool pair = j < K && ridA[s] >= 0 && cj >= 0 && cj != ridA[s];
-                    if (AUDIT && pair) audit_pair(a, ridA[s], cj, d, ndot, nviol);
+                    if (AUDIT && j < K && ridA[s] >= 0 && cj >= 0 && cj != ridA[s])
+                        audit_pair(a, ridA[s], cj, d, ndot, nviol);
                     const float thr = COL ? __fsub_rd(h, mA[s].phi) : mA[s].phi;
-                    const bool pass = pair && d >= thr;
-                    if (pass) sSv[(s * 32 + lane) * L.SVS + q[s]] = d;
-                    q[s] += pass ? 1 : 0;
-                    mk[s] |= (pass ? 1u : 0u) << j;
+                    if (j < K) sSv[(s * 32 + lane) * L.SVS + j] = d;
+                    mk[s] |= (d >= thr && cj != ridA[s]) ? 1u << j : 0u;
                 }
+            }
+        }
+        {
+            // columns 0..K-1 that hold a point (the hub's friend list has no gaps but
+            // a slot may read -1 at the ends of the index range)
+            const unsigned cvalid = __ballot_sync(FULL, lane < K && cid[lane] >= 0);
+#pragma unroll
+            for (int s = 0; s < R; ++s) {
+                mk[s] = ridA[s] >= 0 ? mk[s] & cvalid : 0u;
+                q[s] = __popc(mk[s]);
             }
         }
         // the co-friend pair (x in F(v), y = v): column K, rows of F(v) only (the
@@ -501,7 +510,7 @@ __global__ void __launch_bounds__(128, R == 2 ? 3 : (MP <= 24 ? 5 : 4))
                 if (AUDIT) audit_pair(a, ridA[0], (int)A.v, acc, ndot, nviol);
                 const float hv = COL ? hcol[K] : 0.f;
                 if (acc >= (COL ? __fsub_rd(hv, mA[0].phi) : mA[0].phi)) {
-                    sSv[lane * L.SVS + q[0]] = acc;  // the last survivor of the row
+                    sSv[lane * L.SVS + K] = acc;  // the last survivor of the row
                     ++q[0];
                 }
             }
@@ -563,9 +572,9 @@ __global__ void __launch_bounds__(128, R == 2 ? 3 : (MP <= 24 ? 5 : 4))
             if (rb >= 0) {
                 // survivor qq of row rr: its qq-th passing column, or (past them) the hub itself
                 const unsigned m = sMask[rr];
-                const float d = sSv[rr * L.SVS + qq];
                 const bool colj = qq < __popc(m);
                 const int j = colj ? (int)__fns(m, 0, qq + 1) : K;
+                const float d = sSv[rr * L.SVS + j];
                 const int y = colj ? cid[j] : (int)A.v;
                 // the entry orders the candidates like their keys: -d, or s (co(y)/s - d)
                 a.bent[rb + qq] =

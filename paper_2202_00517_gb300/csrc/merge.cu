@@ -14,10 +14,10 @@
 // candidates with integer compares only (GB300's FP64 pipe is narrow):
 //  1. each lane scans its share of the bucket, drops old friends (per-warp
 //     shared-memory hash) and copies of entries it holds, keeps its R smallest
-//     (u, index), and remembers the smallest u it pushed out;
+//     by u, and remembers the smallest u it pushed out;
 //  2. T, an upper bound of the exact K-th key of the pool: the old K-th key,
-//     or (when more than 32 candidates pass) the bound of the K-th smallest
-//     distinct (u, index) kept, by K rounds of warp argmin;
+//     or (when more than 32 candidates pass) the bound of a u below which at
+//     least K distinct kept candidates lie, by K rounds of warp minimum;
 //  3. if some lane pushed out an entry that could still reach T, the row is
 //     listed (with T) for a second kernel, which streams its bucket again 32
 //     entries at a time and keys and inserts, by the batched insertion, every
@@ -412,43 +412,49 @@ __device__ void serial_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE>
 }
 
 // ------------------------------------------------------------------ fast path
+// A lane's R smallest candidates by u (ties in arrival order), held in
+// registers as 32-bit fields: the threshold extraction reads u alone, so the
+// list needs no 64-bit (u, index) keys.
 template <int R>
 struct LaneTop {
-    uint64_t pk[R];   // (sortable u << 32) | index, ascending; ~0 = empty
-    int pos[R];       // bucket slot of the entry
-    uint32_t drop;    // smallest sortable u pushed out (~0 = none)
+    uint32_t u[R];  // sortable u, ascending; ~0 = empty
+    int y[R];       // candidate index, -1 = empty
+    int pos[R];     // bucket slot of the entry
+    uint32_t drop;  // smallest sortable u pushed out (~0 = none)
 
     __device__ __forceinline__ void init() {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            pk[r] = ~0ull;
+            u[r] = 0xffffffffu;
+            y[r] = -1;
             pos[r] = 0;
         }
         drop = 0xffffffffu;
     }
-    __device__ __forceinline__ void push(uint64_t p, int ps) {
-        if (p >= pk[R - 1]) {
-            drop = min(drop, (uint32_t)(p >> 32));
+    __device__ __forceinline__ void push(uint32_t pu, int py, int ps) {
+        if (pu >= u[R - 1]) {
+            drop = min(drop, pu);
             return;
         }
-        // a copy of an entry this lane already holds (same index, same u) adds nothing
+        // a copy of an entry this lane already holds (same u, same index) adds
+        // nothing; the last entry's u is above pu, so no copy sits there
         bool dup = false;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dup |= (pk[r] == p);
+        for (int r = 0; r < R - 1; ++r) dup |= (u[r] == pu) & (y[r] == py);
         if (dup) return;
-        if (pk[R - 1] != ~0ull) drop = min(drop, (uint32_t)(pk[R - 1] >> 32));
-        bool placed = false;
+        drop = min(drop, u[R - 1]);  // the last entry leaves (~0 when the list was not full)
+        // entry r of the new list: the old entry r - 1 when pu goes before it,
+        // else pu when it goes before the old entry r, else the old entry r
+        bool c[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) c[r] = pu < u[r];
 #pragma unroll
         for (int r = R - 1; r >= 0; --r) {
-            if (placed) continue;
-            if (r > 0 && p < pk[r - 1]) {
-                pk[r] = pk[r - 1];
-                pos[r] = pos[r - 1];
-            } else {
-                pk[r] = p;
-                pos[r] = ps;
-                placed = true;
-            }
+            const int rm = r > 0 ? r - 1 : 0;
+            const bool before = r > 0 && c[rm];
+            u[r] = before ? u[rm] : (c[r] ? pu : u[r]);
+            y[r] = before ? y[rm] : (c[r] ? py : y[r]);
+            pos[r] = before ? pos[rm] : (c[r] ? ps : pos[r]);
         }
     }
 };
@@ -471,11 +477,16 @@ __device__ __forceinline__ void insert_batch(WarpList<1> &X, int K, int lane, ui
 {
     const unsigned FULL = 0xffffffffu;
     bool v = has && lex_less_u(k, ci, xk, xi);
-    if (!__any_sync(FULL, v)) return;
+    const unsigned vm0 = __ballot_sync(FULL, v);
+    if (!vm0) return;
+    // lanes above the highest candidate hold +inf, so the stages that sort blocks of up
+    // to the first power of two above it sort every candidate (in the lowest block)
+    const int top = 31 - __clz(vm0);
     uint64_t ck = v ? k : ~0ull;
     int cj = v ? ci : 0x7fffffff;
 #pragma unroll
     for (int kk = 2; kk <= 32; kk <<= 1) {
+        if ((kk >> 1) > top) break;
 #pragma unroll
         for (int j = kk >> 1; j > 0; j >>= 1) {
             const uint64_t ok = __shfl_xor_sync(FULL, ck, j);
@@ -617,9 +628,9 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
             en[t] = (c0 + 32 * t < cnt) ? a.bent[base + c0 + 32 * t] : make_int2(0, -1);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            if (en[t].y < 0 || en[t].y >= a.n || hash_has(tab, en[t].y)) continue;
+            if ((uint32_t)en[t].y >= (uint32_t)a.n || hash_has(tab, en[t].y)) continue;  // also y < 0
             passing += 1;
-            L.push(((uint64_t)(uint32_t)en[t].x << 32) | (uint32_t)en[t].y, c0 + 32 * t);
+            L.push((uint32_t)en[t].x, en[t].y, c0 + 32 * t);
         }
     }
     const int P = __reduce_add_sync(0xffffffffu, passing);
@@ -629,22 +640,22 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
     X.kth(K, T0, Ti);
     double T = from_dkey(T0);
     if (P > 32) {
-        // the K smallest distinct (u, index) among the lanes' lists, one per step:
-        // the warp minimum of the heads by u, then by index (two single-instruction
-        // warp reductions); every lane holding that candidate pops it (copies of one
-        // candidate sit in different lanes, never twice in one)
+        // the K-th smallest u among the lanes' lists, one u value per step: the warp
+        // minimum of the heads' u (one single-instruction warp reduction), and every
+        // lane whose head has that u pops it.  The steps spent at one value w number
+        // the most entries of u = w that one lane holds, never more than the distinct
+        // candidates of u = w (a lane holds no candidate twice), so after K steps at
+        // least K distinct candidates have u <= mu: T bounds the K-th key from above
         int popped = 0, count = 0;
         uint32_t mu = 0xffffffffu;
         while (count < K) {
-            uint64_t head = ~0ull;
+            uint32_t hu = 0xffffffffu;
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                if (r == popped) head = L.pk[r];
-            const uint32_t hu = (uint32_t)(head >> 32), hi = (uint32_t)head;
+                if (r == popped) hu = L.u[r];
             mu = __reduce_min_sync(0xffffffffu, hu);
             if (mu == 0xffffffffu) break;  // every list exhausted
-            const uint32_t mi = __reduce_min_sync(0xffffffffu, hu == mu ? hi : 0xffffffffu);
-            if (hu == mu && hi == mi) popped += 1;
+            popped += (hu == mu) ? 1 : 0;
             count += 1;
         }
         if (count == K) T = fmin(T, B.upper(from_sortable_bits(mu)));
@@ -659,9 +670,9 @@ __device__ bool fast_row(const MergeArgs &a, int64_t x, int lane, WarpList<NE> &
     int nlive = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const bool live = L.pk[r] != ~0ull && (uint32_t)(L.pk[r] >> 32) <= reach;
+        const bool live = L.y[r] >= 0 && L.u[r] <= reach;
         const unsigned mask = __ballot_sync(0xffffffffu, live);
-        if (live) live_list[nlive + __popc(mask & lt)] = make_int2((int)(uint32_t)L.pk[r], L.pos[r]);
+        if (live) live_list[nlive + __popc(mask & lt)] = make_int2(L.y[r], L.pos[r]);
         nlive += __popc(mask);
     }
     __syncwarp();
