@@ -45,13 +45,13 @@ void drop_loop_graph(knnd_handle *h);
 
 void free_all(knnd_handle *h)
 {
-    void *ptrs[] = {h->X64,      h->L64,        h->negH,    h->nx,         h->X32,      h->L32,
-                    h->smax_bits, h->err,        h->deg,     h->slot,       h->heavy_items, h->heavy_nitems,
-                    h->cof_off,  h->cof,        h->cof_new, h->flag_tmp,   h->scan_tmp, h->tau,
-                    h->idxK,     h->meta,       h->Ex,      h->bcnt,       h->bkey,     h->bent,
-                    h->fb_list,  h->fb_T,       h->join_queue, h->fb_count, h->cnt,     h->pts_dev,
-                    h->idx_dev,  h->key_dev,    h->idxA,    h->keyA,       h->flagA,    h->inst_of,
-                    h->inst_base, h->inst_n,    h->inst_seed, h->inst_active, h->inst_cnt};
+    void *ptrs[] = {h->X64,       h->L64,      h->negH,      h->nx,          h->X32,         h->L32,
+                    h->smax_bits, h->err,      h->deg,       h->deg_mut,     h->slot,        h->heavy_items,
+                    h->heavy_nitems, h->cof_off, h->cof,     h->cof_new,     h->flag_tmp,    h->scan_tmp,
+                    h->tau,       h->idxK,     h->meta,      h->Ex,          h->bcnt,        h->bkey,
+                    h->bent,      h->fb_list,  h->fb_T,      h->join_queue,  h->fb_count,    h->cnt,
+                    h->pts_dev,   h->idx_dev,  h->key_dev,   h->idxA,        h->keyA,        h->flagA,
+                    h->inst_of,   h->inst_base, h->inst_n,   h->inst_seed,   h->inst_active, h->inst_cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->cnt_host) cudaFreeHost(h->cnt_host);
@@ -159,6 +159,8 @@ knnd_status do_round(knnd_handle *h, uint64_t seed, int32_t round, int32_t *idx,
     // incremental proposals read the flags of G_{r-1} (the join runs before the
     // merge overwrites them with those of G_r)
     h->round_flag = (h->prm.incremental && newflag) ? newflag : nullptr;
+    // the random graph G_0 has almost no mutual friends: round 1 skips their search
+    h->csr_mutual = round >= 2;
     // one instance: the hubs [0, n / den) then the rest; several instances
     // (batched form): each instance's first n_i / den hubs, then the rest
     const int64_t den = h->split_den;
@@ -461,6 +463,7 @@ knnd_status make_handle(knnd_handle **out, const Caps &c, knnd_dtype dtype, knnd
     if (!s) s = dalloc(h, &h->smax_bits, 3 * (c.ninst > 0 ? c.ninst : 1));
     if (!s) s = dalloc(h, &h->err, 1);
     if (!s) s = dalloc(h, &h->deg, n);
+    if (!s) s = dalloc(h, &h->deg_mut, n);
     if (!s) s = dalloc(h, &h->slot, c.nK);
     if (!s) s = dalloc(h, &h->heavy_items, c.nK / 64 + 16);
     if (!s) s = dalloc(h, &h->heavy_nitems, 1);

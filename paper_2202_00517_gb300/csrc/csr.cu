@@ -50,20 +50,46 @@ __device__ __forceinline__ void row_thresholds(int64_t x, double t, int32_t v, d
     }
 }
 
-// One thread per arc e = x*K + t (x -> idx[e]).
+// x in F(v)?  f: v's friend list (K entries).
+__device__ __forceinline__ bool friend_of(const int32_t *__restrict__ f, int K, int32_t x)
+{
+    bool hit = false;
+    if ((K & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {  // 16-byte aligned rows
+        const int4 *f4 = reinterpret_cast<const int4 *>(f);
+        for (int q = 0; q < K / 4; ++q) {
+            const int4 t = f4[q];
+            hit |= (t.x == x) | (t.y == x) | (t.z == x) | (t.w == x);
+        }
+    } else {
+        for (int q = 0; q < K; ++q) hit |= f[q] == x;
+    }
+    return hit;
+}
+
+// One thread per arc e = x*K + t (x -> idx[e]).  With deg_mut (the TMA join's
+// rows): a co-friend x of v that is also a friend of v (x in F(v) and v in
+// F(x)) stands twice among the hub's rows, F(v) followed by coF(v), and its
+// second row proposes exactly the pairs (x, y), y in F(v), of its first; the
+// pool of Sec. 3.1 is a set, so the copy adds nothing.  Such arcs are counted
+// in deg_mut and placed at the end of coF(v), the others in deg at its front:
+// the TMA join reads the first deg[v] entries, every other consumer the whole
+// list (the same set of pairs either way).
 __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *__restrict__ key, int64_t n, int K,
                                  int32_t *__restrict__ deg, int32_t *__restrict__ slot, double *__restrict__ tau,
                                  int32_t *__restrict__ idxK,
                                  const double *__restrict__ negH, const double *__restrict__ nx,
                                  const unsigned long long *__restrict__ smax_bits, InstView iv, double bound_c,
                                  int cmp,
-                                 RowMeta *__restrict__ meta, double *__restrict__ Ex, int32_t *err)
+                                 RowMeta *__restrict__ meta, double *__restrict__ Ex, int32_t *err,
+                                 int32_t *__restrict__ deg_mut)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * K) return;
     const int32_t v = idx[e];
     if (v < 0 || v >= n) {
         atomicOr(err, kErrIndex);
+    } else if (deg_mut && friend_of(idx + (int64_t)v * K, K, (int32_t)(e / K))) {
+        slot[e] = -1 - atomicAdd(&deg_mut[v], 1);  // from the end of coF(v)
     } else {
         slot[e] = atomicAdd(&deg[v], 1);  // the arc's position in coF(v)
     }
@@ -118,12 +144,13 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *tota
     return r;
 }
 
-__global__ void scan_tiles_kernel(const int32_t *__restrict__ deg, int64_t n, int64_t *__restrict__ tile_sum)
+__global__ void scan_tiles_kernel(const int32_t *__restrict__ deg, const int32_t *__restrict__ deg_mut, int64_t n,
+                                  int64_t *__restrict__ tile_sum)
 {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
     int64_t s = 0;
     for (int i = 0; i < kScanPer; ++i)
-        if (base + i < n) s += deg[base + i];
+        if (base + i < n) s += deg[base + i] + (deg_mut ? deg_mut[base + i] : 0);
     __shared__ int64_t tot;
     block_exclusive_scan(s, &tot);
     if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
@@ -145,14 +172,15 @@ __global__ void scan_sums_kernel(int64_t *__restrict__ tile_sum, int64_t ntiles,
     if (threadIdx.x == 0) off[n] = carry;
 }
 
-__global__ void scan_apply_kernel(const int32_t *__restrict__ deg, int64_t n, const int64_t *__restrict__ tile_off,
+__global__ void scan_apply_kernel(const int32_t *__restrict__ deg, const int32_t *__restrict__ deg_mut, int64_t n,
+                                  const int64_t *__restrict__ tile_off,
                                   int64_t *__restrict__ off, RowMeta *__restrict__ meta, int K)
 {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
     int64_t v[kScanPer];
     int64_t s = 0;
     for (int i = 0; i < kScanPer; ++i) {
-        v[i] = (base + i < n) ? deg[base + i] : 0;
+        v[i] = (base + i < n) ? deg[base + i] + (deg_mut ? deg_mut[base + i] : 0) : 0;
         s += v[i];
     }
     __shared__ int64_t tot;
@@ -178,7 +206,8 @@ __global__ void csr_fill_kernel(const int32_t *__restrict__ idx, const int32_t *
     if (e >= n * K) return;
     const int32_t v = idx[e];
     if (v < 0 || v >= n) return;
-    const int64_t q = off[v] + slot[e];
+    const int32_t sl = slot[e];
+    const int64_t q = sl >= 0 ? off[v] + sl : off[v + 1] + sl;  // mutual arcs from the end
     cof[q] = (int32_t)(e / K);
     if (flag) cof_new[q] = flag[e];
 }
@@ -191,17 +220,19 @@ cudaError_t launch_reverse_csr(knnd_handle *h, const int32_t *idx, const double 
     const int threads = 256;
     const unsigned eblocks = (unsigned)((E + threads - 1) / threads);
     cudaMemsetAsync(h->deg, 0, sizeof(int32_t) * n, h->stream);
+    int32_t *deg_mut = (h->csr_mutual && join_runs_tma(h)) ? h->deg_mut : nullptr;  // mutual arcs apart
+    if (deg_mut) cudaMemsetAsync(deg_mut, 0, sizeof(int32_t) * n, h->stream);
     const bool mixed = h->prec != KNND_PREC_FP64;
     csr_count_kernel<<<eblocks, threads, 0, h->stream>>>(idx, key, n, K, h->deg, h->slot, h->tau, h->idxK, h->negH,
                                                          h->nx,
                                                          h->smax_bits, h->iv, h->bound_c, h->prm.comparator,
                                                          mixed ? h->meta : nullptr,
-                                                         h->Ex, h->err);
+                                                         h->Ex, h->err, deg_mut);
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
-    scan_tiles_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp);
+    scan_tiles_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, deg_mut, n, h->scan_tmp);
     scan_sums_kernel<<<1, kScanThreads, 0, h->stream>>>(h->scan_tmp, ntiles, h->cof_off, n);
-    scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, n, h->scan_tmp, h->cof_off,
-                                                                        mixed ? h->meta : nullptr, K);
+    scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, h->stream>>>(h->deg, deg_mut, n, h->scan_tmp,
+                                                                        h->cof_off, mixed ? h->meta : nullptr, K);
     csr_fill_kernel<<<eblocks, threads, 0, h->stream>>>(idx, h->slot, n, K, h->cof_off, h->cof, h->round_flag,
                                                         h->cof_new);
     h->launches += 5;

@@ -755,13 +755,23 @@ static cudaError_t run_join_cpl(knnd_handle *h, const JoinArgs &a)
     return run_join<MP, 2>(h, a);
 }
 
+static bool join_runs_tc(const knnd_handle *h)
+{
+    return h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && h->prm.comparator == KNND_CMP_KL;
+}
+
+bool join_runs_tma(const knnd_handle *h)
+{
+    return !join_runs_tc(h) && h->join_form == KNND_JOIN_TMA && tma_join_supported(h);
+}
+
 cudaError_t launch_join(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase, int split_den)
 {
-    if (h->prec == KNND_PREC_MIXED_BF16X3 && tc_supported(h->MP, h->K) && h->prm.comparator == KNND_CMP_KL) {
+    if (join_runs_tc(h)) {
         h->join_kernel = KNND_JOIN_TC;
         return launch_join_tc(h, idx, h_lo, h_hi, phase, split_den);
     }
-    if (h->join_form == KNND_JOIN_TMA && tma_join_supported(h)) {
+    if (join_runs_tma(h)) {
         cudaMemsetAsync(h->bcnt, 0, sizeof(int32_t) * h->n, h->stream);
         h->launches += 1;
         h->join_kernel = KNND_JOIN_TMA;

@@ -4,7 +4,10 @@
 // Same hub tiles, filter, bucket entries and error bound as join_mixed_kernel
 // (join.cu): hub v's rows are F(v) then coF(v), its columns F(v) and, for the
 // rows of F(v), v itself; a pair is kept when its FP32 dot can still beat the
-// row's K-th entry.  What differs is how the tile reaches the FP32 pipe:
+// row's K-th entry.  Here the co-friends that are also friends of v are left
+// out of the rows (their pairs are those of their first row; launch_reverse_csr
+// places them last in each list).  What differs besides is how the tile reaches the FP32
+// pipe:
 //
 //  * a warp takes a hub's rows 32 R at a time (an item; R = 1 is the one
 //    instantiated); lane t owns row t of the item (and t + 32 when R = 2) for
@@ -57,6 +60,7 @@ struct TmaJoinArgs {
     int K, MP;
     const int32_t *idx;
     const int64_t *cof_off;
+    const int32_t *ncof;  // per hub: the co-friends that are no friends, at the front of its list
     const int32_t *cof;
     const RowMeta *meta;
     const double *negH;  // column offsets (comparators with one)
@@ -171,7 +175,7 @@ constexpr int kChunk = 32;
 
 struct HubWalk {
     int64_t next, end;  // the claimed chunk [next, end)
-    int64_t c0, c1;     // cof_off[next], cof_off[next + 1] (when next < h_hi)
+    int64_t c0, c1;     // cof_off[next], and the end of its co-friends that are no friends (when next < h_hi)
 };
 
 // Called by all lanes of the warp together.
@@ -188,7 +192,7 @@ __device__ __forceinline__ void walk_load(const TmaJoinArgs &a, HubWalk &w)
 {
     if (w.next < a.h_hi) {
         w.c0 = a.cof_off[w.next];
-        w.c1 = a.cof_off[w.next + 1];
+        w.c1 = w.c0 + a.ncof[w.next];
     }
 }
 
@@ -693,6 +697,7 @@ cudaError_t launch_join_tma(knnd_handle *h, const int32_t *idx, int64_t h_lo, in
     a.MP = h->MP;
     a.idx = idx;
     a.cof_off = h->cof_off;
+    a.ncof = h->deg;  // the front of each coF(v) that launch_reverse_csr kept for this join
     a.cof = h->cof;
     a.meta = h->meta;
     a.negH = h->negH;

@@ -200,7 +200,8 @@ struct knnd_handle {
     unsigned long long *smax_bits;
     int32_t *err;                   // device error word
     // reverse CSR
-    int32_t *deg;     // n: in-degree
+    int32_t *deg;     // n: in-degree; for the TMA join, |coF(v) \ F(v)| (those entries first in coF(v))
+    int32_t *deg_mut; // n: for the TMA join, |coF(v) & F(v)| (those entries last in coF(v))
     int32_t *slot;    // n*K: each arc's position in its co-friend list
     // the mixed join's heavy hubs: items (hub, row group) and their count;
     // capacity nK/64 + 16 >= 2nK/256 + 2nK/1025 (rows over all hubs: 2nK)
@@ -214,6 +215,7 @@ struct knnd_handle {
     uint8_t *cof_new;   // n*K
     uint8_t *flag_tmp;  // n*K
     const uint8_t *round_flag;
+    bool csr_mutual;  // this round's CSR puts the mutual arcs apart (for the TMA join)
     int64_t *scan_tmp;
     int64_t scan_tmp_len;
     // per-row thresholds of the join filter
@@ -299,6 +301,9 @@ cudaError_t launch_join_tc(knnd_handle *h, const int32_t *idx, int64_t h_lo, int
 // The FP32 join with TMA-gathered rows and columns (join_tma.cu): the default
 // mixed-form join where tma_join_supported(h) holds.
 bool tma_join_supported(const knnd_handle *h);
+// The join of the next launch_join is the TMA join (its rows skip the
+// co-friends that are also friends: launch_reverse_csr puts them last in coF).
+bool join_runs_tma(const knnd_handle *h);
 cudaError_t launch_join_tma(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase,
                             int split_den);
 double bound_c_bf16x3(int MP);

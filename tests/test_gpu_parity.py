@@ -186,18 +186,29 @@ def test_lockstep_all_pairs_proposed(knnd, prec):
 def test_incremental_proposals_same_graph(knnd, n, m, K):
     # a pair met only through arcs of the previous round's graph is not proposed
     # again: the build is the same, bit for bit, with fewer candidates merged
+    # The TMA join takes no incremental proposals, so in the mixed form both builds
+    # join with plain loads (the survivor counts then compare like with like), and
+    # the full pool joined by TMA must give the same graph as well.
     seed = 4
     pts = _dev(dirichlet_points(n, m, seed, np.float32))
-    for prec in PRECS:
+    for prec in ("fp64", "mixed", "bf16x3"):
         res = {}
         for inc in (False, True):
-            h = _handle(knnd, n, m, K, dtype="f32", precision=prec, incremental=inc)
+            kw = {"join_form": "plain"} if prec == "mixed" else {}
+            h = _handle(knnd, n, m, K, dtype="f32", precision=prec, incremental=inc, **kw)
             res[inc] = h.build(pts, seed)
             h.close()
         a, b = res[False], res[True]
         assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"], prec
         assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["key"], b["key"]), prec
         assert b["join_survivors"] < a["join_survivors"], prec
+        if prec == "mixed":
+            h = _handle(knnd, n, m, K, dtype="f32", precision="mixed_tma")
+            c = h.build(pts, seed)
+            h.close()
+            assert c["join_kernel"] == ("tma" if m < 32 and K <= 32 else "plain"), prec  # TMA: m + 1 <= 32
+            assert c["updates"] == b["updates"], prec
+            assert torch.equal(c["idx"], b["idx"]) and torch.equal(c["key"], b["key"]), prec
 
 
 @pytest.mark.parametrize("n,m,K", [(200_000, 21, 20), (60_000, 65, 32), (50_000, 11, 32)])
