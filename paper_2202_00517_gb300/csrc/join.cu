@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
         const int idB = (active && cB < K) ? sCid[cB] : -1;
         // MP = 128: two columns' log rows do not fit in registers; the scoring runs
         // over CHK coordinates at a time, the partial dots carried in the dot buffer
-        // (the same fma chain, in the same order)
+        // (each chunk's two chains start from the partial dot and zero)
         constexpr int CHK = MP <= 96 ? MP : 32;
         constexpr int NCH = MP / CHK;
         float LA[CHK], LB[CHK];
@@ -383,36 +383,43 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
                     const int r1 = r0 + 1;  // row 32 of sX is the hub row: harmless when r1 == nr
                     const float4 *x0 = reinterpret_cast<const float4 *>(sX + r0 * S::RS) + ch * (CHK / 4);
                     const float4 *x1 = reinterpret_cast<const float4 *>(sX + r1 * S::RS) + ch * (CHK / 4);
-                    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+                    // each dot as two chains, over the even and the odd coordinates, run
+                    // together by packed two-wide fmas and added at the end of the chunk
+                    // (the co-friend pair below follows the same order)
+                    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
                     if (ch > 0) {  // this lane's own cells of the previous chunk
                         if (cA < K) {
-                            a0 = sD[r0 * DS + cA];
-                            if (r1 < nr) a1 = sD[r1 * DS + cA];
+                            a0.x = sD[r0 * DS + cA];
+                            if (r1 < nr) a1.x = sD[r1 * DS + cA];
                         }
                         if (cB < K) {
-                            b0 = sD[r0 * DS + cB];
-                            if (r1 < nr) b1 = sD[r1 * DS + cB];
+                            b0.x = sD[r0 * DS + cB];
+                            if (r1 < nr) b1.x = sD[r1 * DS + cB];
                         }
                     }
 #pragma unroll
                     for (int i4 = 0; i4 < CHK / 4; ++i4) {
                         const float4 u = x0[i4], w = x1[i4];
-                        a0 = __fmaf_rn(u.x, LA[4 * i4 + 0], a0); a1 = __fmaf_rn(w.x, LA[4 * i4 + 0], a1);
-                        b0 = __fmaf_rn(u.x, LB[4 * i4 + 0], b0); b1 = __fmaf_rn(w.x, LB[4 * i4 + 0], b1);
-                        a0 = __fmaf_rn(u.y, LA[4 * i4 + 1], a0); a1 = __fmaf_rn(w.y, LA[4 * i4 + 1], a1);
-                        b0 = __fmaf_rn(u.y, LB[4 * i4 + 1], b0); b1 = __fmaf_rn(w.y, LB[4 * i4 + 1], b1);
-                        a0 = __fmaf_rn(u.z, LA[4 * i4 + 2], a0); a1 = __fmaf_rn(w.z, LA[4 * i4 + 2], a1);
-                        b0 = __fmaf_rn(u.z, LB[4 * i4 + 2], b0); b1 = __fmaf_rn(w.z, LB[4 * i4 + 2], b1);
-                        a0 = __fmaf_rn(u.w, LA[4 * i4 + 3], a0); a1 = __fmaf_rn(w.w, LA[4 * i4 + 3], a1);
-                        b0 = __fmaf_rn(u.w, LB[4 * i4 + 3], b0); b1 = __fmaf_rn(w.w, LB[4 * i4 + 3], b1);
+                        const float2 la0 = make_float2(LA[4 * i4 + 0], LA[4 * i4 + 1]);
+                        const float2 la1 = make_float2(LA[4 * i4 + 2], LA[4 * i4 + 3]);
+                        const float2 lb0 = make_float2(LB[4 * i4 + 0], LB[4 * i4 + 1]);
+                        const float2 lb1 = make_float2(LB[4 * i4 + 2], LB[4 * i4 + 3]);
+                        a0 = __ffma2_rn(make_float2(u.x, u.y), la0, a0);
+                        a1 = __ffma2_rn(make_float2(w.x, w.y), la0, a1);
+                        b0 = __ffma2_rn(make_float2(u.x, u.y), lb0, b0);
+                        b1 = __ffma2_rn(make_float2(w.x, w.y), lb0, b1);
+                        a0 = __ffma2_rn(make_float2(u.z, u.w), la1, a0);
+                        a1 = __ffma2_rn(make_float2(w.z, w.w), la1, a1);
+                        b0 = __ffma2_rn(make_float2(u.z, u.w), lb1, b0);
+                        b1 = __ffma2_rn(make_float2(w.z, w.w), lb1, b1);
                     }
                     if (cA < K) {
-                        sD[r0 * DS + cA] = a0;
-                        if (r1 < nr) sD[r1 * DS + cA] = a1;
+                        sD[r0 * DS + cA] = __fadd_rn(a0.x, a0.y);
+                        if (r1 < nr) sD[r1 * DS + cA] = __fadd_rn(a1.x, a1.y);
                     }
                     if (cB < K) {
-                        sD[r0 * DS + cB] = b0;
-                        if (r1 < nr) sD[r1 * DS + cB] = b1;
+                        sD[r0 * DS + cB] = __fadd_rn(b0.x, b0.y);
+                        if (r1 < nr) sD[r1 * DS + cB] = __fadd_rn(b1.x, b1.y);
                     }
                 }
             }
@@ -440,14 +447,20 @@ __global__ void __launch_bounds__(128, mixed_min_blocks(MP)) join_mixed_kernel(J
             if (r < K && rid >= 0 && (!INC || rnew)) {
                 const float4 *xr = reinterpret_cast<const float4 *>(sX + lane * S::RS);
                 const float4 *lv = reinterpret_cast<const float4 *>(sX + 32 * S::RS);
+                // the scoring's order (chunks of CHK, two chains each): the same pair met
+                // at another hub as row and column gets the same FP32 value, so that the
+                // merge recognises the copies of one candidate
                 float acc = 0.f;
 #pragma unroll
-                for (int i4 = 0; i4 < MP / 4; ++i4) {
-                    const float4 xv = xr[i4], lw = lv[i4];
-                    acc = __fmaf_rn(xv.x, lw.x, acc);
-                    acc = __fmaf_rn(xv.y, lw.y, acc);
-                    acc = __fmaf_rn(xv.z, lw.z, acc);
-                    acc = __fmaf_rn(xv.w, lw.w, acc);
+                for (int ch = 0; ch < NCH; ++ch) {
+                    float2 e = make_float2(acc, 0.f);
+#pragma unroll
+                    for (int i4 = ch * (CHK / 4); i4 < (ch + 1) * (CHK / 4); ++i4) {
+                        const float4 xv = xr[i4], lw = lv[i4];
+                        e = __ffma2_rn(make_float2(xv.x, xv.y), make_float2(lw.x, lw.y), e);
+                        e = __ffma2_rn(make_float2(xv.z, xv.w), make_float2(lw.z, lw.w), e);
+                    }
+                    acc = __fadd_rn(e.x, e.y);
                 }
                 cfd = acc;
                 cfpass = acc >= (COL ? __fsub_rd(hv, ph) : ph);

@@ -499,7 +499,9 @@ __global__ void __launch_bounds__(128, R == 2 ? 3 : (MP <= 24 ? 5 : 4))
             }
         }
         // the co-friend pair (x in F(v), y = v): column K, rows of F(v) only (the
-        // hub's first K rows: lanes < K of the first item's first rows)
+        // hub's first K rows: lanes < K of the first item's first rows), in the same
+        // fma order as the columns above, so that a pair met again at another hub
+        // gets the same FP32 value and the merge sees its copies as one candidate
         if (A.ch == 0) {
             const float4 *cv = Cb + K * (MP / 4);
             float2 e = make_float2(0.f, 0.f);
