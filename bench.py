@@ -413,7 +413,8 @@ def gpu_single(args, name, rank, world, local, barrier):
     compulsory = 2.0 * N * MP * 4 + 2.0 * N * K * 4 + 8.0 * (N + 1) + 16.0 * N + 8.0 * surv_t / join_n
     tma = info.get("join_kernel") == "tma"
     if tma:
-        kname, traffic = f"join_tma_kernel<{MP}, 0, 0>", join_traffic_per_launch(name, "join_tma.cu", "join_tma")
+        kname = f"join_tma_kernel<{MP}, 0, 0>" if MP <= 32 else f"join_wide_kernel<{MP}, 0>"
+        traffic = join_traffic_per_launch(name, "join_tma.cu", "join_tma")
     elif args.form == "mixed":
         kname, traffic = f"join_mixed_kernel<{MP}, 0, 0, 0>", join_traffic_per_launch(name)
     else:
@@ -557,7 +558,8 @@ def gpu_leg(args, name, local, steps=2, warmup=1):
                      "rescored_per_build": r["rescored"],
                      "join_ms_per_launch": st["phase_ms"]["join"] / max(1, st["phase_count"]["join"]),
                      "merge_ms_per_launch": st["phase_ms"]["merge"] / max(1, st["phase_count"]["merge"]),
-                     "join_kernel": {"tma": f"join_tma_kernel<{pad_m(m)}, 0, 0>",
+                     "join_kernel": {"tma": (f"join_tma_kernel<{pad_m(m)}, 0, 0>" if pad_m(m) <= 32
+                                             else f"join_wide_kernel<{pad_m(m)}, 0>"),
                                      "plain": f"join_mixed_kernel<{pad_m(m)}, 0, 0, 0>",
                                      "tc": f"join_tc_kernel<{pad_m(m)}>"}.get(r["join_kernel"], r["join_kernel"])}
     a, b = res["mixed"], res["bf16x3"]

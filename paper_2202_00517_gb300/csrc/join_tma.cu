@@ -611,6 +611,289 @@ __global__ void __launch_bounds__(128, R == 2 ? 3 : (MP <= 24 ? 5 : 4))
     }
 }
 
+// ------------------------------------------------------------------ wide rows
+// join_wide_kernel: the same filter for 41..72 real coordinates (MP 48, 64 or
+// 72; K <= 32).  One row per lane would hold MP coordinates in registers and
+// read every column coordinate once for one row.  Here, as in join_mixed_kernel
+// (join.cu), lane (g, p) holds the log rows of columns 2p and 2p + 1 in
+// registers and reads each coordinate of rows 2g + 2Gi and 2g + 2Gi + 1 (G row
+// groups) once for both columns: half the shared-memory reads per fma at these
+// widths.  What the TMA adds to that layout: an item's 32 rows and a hub's K + 1
+// columns reach shared memory by tile::gather4, so the load/store pipe carries
+// no gathered sectors, and the next item's copies (its rows; for a new hub also
+// its columns) are in flight while the current item's dots are filtered and
+// written.  The dots are the same two fma chains (even and odd coordinates,
+// added at the end) as every other FP32 join form, the co-friend pair included,
+// so that copies of a pair met at several hubs carry one FP32 value.
+struct WideLayout {
+    int MP, K, KC, DS;
+    int off_row, off_col, off_dot, off_cid, off_h, off_inc, off_rb, off_mask, off_bar, bytes;
+    __host__ __device__ WideLayout(int mp, int k, bool col) : MP(mp), K(k)
+    {
+        KC = (K + 1 + 3) & ~3;                 // columns: F(v), then v, padded to whole gather4s
+        DS = (K + 1) | 1;                      // dots of a row: K columns, then the co-friend pair
+        off_row = 0;                           // [32][MP] the item's rows
+        off_col = off_row + 32 * MP * 4;       // [KC][MP] the hub's columns (multiples of 128 bytes)
+        off_dot = off_col + KC * MP * 4;       // [32][DS] the item's dots
+        off_cid = off_dot + ((32 * DS * 4 + 15) & ~15);
+        off_h = off_cid + 2 * kSlot * 4;       // [2][kSlot] column ids; COL: RD(co(y) / s)
+        off_inc = off_h + (col ? 2 * kSlot * 4 : 0);
+        off_rb = off_inc + 32 * 4;
+        off_mask = off_rb + 32 * 8;
+        off_bar = off_mask + 32 * 4;
+        bytes = (off_bar + 2 * 8 + 127) & ~127;
+    }
+};
+
+template <int MP, bool COL>
+__global__ void __launch_bounds__(128, 2) join_wide_kernel(const __grid_constant__ TmaJoinArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = a.K;
+    const WideLayout L(MP, K, COL);
+    unsigned char *wb = smem_tma + (size_t)warp * L.bytes;
+    const float4 *sRow4 = reinterpret_cast<const float4 *>(wb + L.off_row);
+    const float4 *sCol4 = reinterpret_cast<const float4 *>(wb + L.off_col);
+    float *sD = reinterpret_cast<float *>(wb + L.off_dot);
+    int *sCid = reinterpret_cast<int *>(wb + L.off_cid);
+    float *sH = reinterpret_cast<float *>(wb + L.off_h);
+    int *sInc = reinterpret_cast<int *>(wb + L.off_inc);
+    long long *sRB = reinterpret_cast<long long *>(wb + L.off_rb);
+    unsigned *sMask = reinterpret_cast<unsigned *>(wb + L.off_mask);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wb + L.off_bar);
+    const uint32_t bar_row = saddr(bars), bar_col = bar_row + 8u;
+    const uint32_t row_dst = saddr(wb + L.off_row), col_dst = saddr(wb + L.off_col);
+    const uint32_t row_bytes = 32u * MP * 4u, col_bytes = (uint32_t)L.KC * MP * 4u;
+    if (saddr(smem_tma) & 127u) {  // the copies need 128-byte aligned destinations (reported as a failed wait)
+        if (lane == 0) atomicOr(a.err, kErrTimeout);
+        return;
+    }
+    if (lane == 0) {
+        for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bars + b)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncwarp();
+    // scoring roles: lane (g, p) = columns 2p, 2p + 1 of row group g
+    const int npairs = (K + 1) >> 1, G = 32 / npairs;
+    const int g = lane / npairs, pr = lane - g * npairs;
+    const bool active = g < G;
+    const int cA = 2 * pr, cB = 2 * pr + 1;
+
+    HubWalk walk;
+    walk.c0 = walk.c1 = 0;
+    walk_claim(a, walk);
+    walk_load(a, walk);
+    Item none;
+    none.valid = false;
+    none.v = none.c0 = 0;
+    none.nrows = none.ch = 0;
+
+    // Copies of item `it` (this lane's id `rid` is row `lane` of the item): its 32
+    // rows; with `cols` (the hub's first item) also the hub's K + 1 columns, the
+    // first K rows and then v, with their ids into column-id slot `slot`.
+    auto issue = [&](const Item &it, int rid, bool cols, int slot) {
+        if (cols) {
+            if (lane < K) sCid[slot * kSlot + lane] = rid;
+            if (lane == 0) sCid[slot * kSlot + K] = (int)it.v;
+            if (COL) {
+                if (lane < K) sH[slot * kSlot + lane] = rid >= 0 ? __double2float_rd(a.negH[rid] * a.col_inv) : 0.f;
+                if (lane == 0) sH[slot * kSlot + K] = __double2float_rd(a.negH[it.v] * a.col_inv);
+            }
+        }
+        // lanes 0..7 gather rows 4l..4l+3, lanes 8..8+KC/4-1 the columns 4(l-8)..4(l-8)+3
+        const int gq = lane < 8 ? lane : lane - 8;
+        int q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 4 * gq + i;
+            const int v = __shfl_sync(FULL, rid, r & 31);
+            q[i] = lane < 8 ? v : (r < K ? v : (r == K ? (int)it.v : -1));
+        }
+        __syncwarp();  // every lane's reads of the buffers come before the copies below
+        if (lane == 0) {
+            expect_bytes(bar_row, row_bytes);
+            if (cols) expect_bytes(bar_col, col_bytes);
+        }
+        __syncwarp();
+        if (lane < 8) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            gather4(row_dst + (uint32_t)(lane * 4 * MP * 4), &a.tm_row, q[0], q[1], q[2], q[3], bar_row);
+        } else if (cols && lane < 8 + L.KC / 4) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            gather4(col_dst + (uint32_t)((lane - 8) * 4 * MP * 4), &a.tm_col, q[0], q[1], q[2], q[3], bar_col);
+        }
+    };
+
+    Item A = next_item(a, none, walk, 32);
+    if (!A.valid) return;
+    int ridA = check_id(a, load_id(a, A, lane, 32), has_row(A, lane, 32));
+    int slotA = 0;
+    issue(A, ridA, true, slotA);  // the first item of a hub
+    uint32_t prow = 0, pcol = 0;   // phase parities of the row and the column barrier
+    float2 LA[MP / 2], LB[MP / 2];  // log rows of columns cA and cB, coordinates (2i, 2i + 1)
+#pragma unroll
+    for (int i = 0; i < MP / 2; ++i) LA[i] = LB[i] = make_float2(0.f, 0.f);
+
+    while (A.valid) {
+        // the next item's ids and this item's row records, in flight during the scoring
+        const Item B = next_item(a, A, walk, 32);
+        int ridB = load_id(a, B, lane, 32);
+        RowMeta mA;
+        mA.phi = 0.f;
+        mA.boff = 0;
+        if (ridA >= 0) mA = a.meta[ridA];
+        const int *cid = sCid + slotA * kSlot;
+        const float *hcol = sH + slotA * kSlot;
+        // 1. a new hub: its columns into registers
+        if (A.ch == 0) {
+            if (!wait_phase(bar_col, pcol, kTmaWaitNs)) {
+                atomicOr(a.err, kErrTimeout);
+                wait_phase(bar_row, prow, kTmaWaitNs);
+                return;
+            }
+            pcol ^= 1u;
+            const float4 *ca = sCol4 + (cA < K ? cA : 0) * (MP / 4);
+            const float4 *cb = sCol4 + (cB < K ? cB : 0) * (MP / 4);
+#pragma unroll
+            for (int i4 = 0; i4 < MP / 4; ++i4) {
+                const float4 ta = ca[i4], tb = cb[i4];
+                LA[2 * i4] = make_float2(ta.x, ta.y);
+                LA[2 * i4 + 1] = make_float2(ta.z, ta.w);
+                LB[2 * i4] = make_float2(tb.x, tb.y);
+                LB[2 * i4 + 1] = make_float2(tb.z, tb.w);
+            }
+        }
+        // 2. the item's rows
+        if (!wait_phase(bar_row, prow, kTmaWaitNs)) {
+            atomicOr(a.err, kErrTimeout);
+            return;
+        }
+        prow ^= 1u;
+        const int nr = min(32, A.nrows - A.ch * 32);
+        // 3. dots of rows r0 and r0 + 1 of group g with columns cA and cB: two chains
+        //    each, over the even and the odd coordinates, added at the end
+        if (active) {
+            for (int r0 = 2 * g; r0 < nr; r0 += 2 * G) {
+                const int r1 = r0 + 1;  // r0 is even and below 31: row r1 is in the buffer
+                const float4 *x0 = sRow4 + r0 * (MP / 4), *x1 = x0 + MP / 4;
+                float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+#pragma unroll
+                for (int i4 = 0; i4 < MP / 4; ++i4) {
+                    const float4 u = x0[i4], w = x1[i4];
+                    a0 = __ffma2_rn(make_float2(u.x, u.y), LA[2 * i4], a0);
+                    a1 = __ffma2_rn(make_float2(w.x, w.y), LA[2 * i4], a1);
+                    b0 = __ffma2_rn(make_float2(u.x, u.y), LB[2 * i4], b0);
+                    b1 = __ffma2_rn(make_float2(w.x, w.y), LB[2 * i4], b1);
+                    a0 = __ffma2_rn(make_float2(u.z, u.w), LA[2 * i4 + 1], a0);
+                    a1 = __ffma2_rn(make_float2(w.z, w.w), LA[2 * i4 + 1], a1);
+                    b0 = __ffma2_rn(make_float2(u.z, u.w), LB[2 * i4 + 1], b0);
+                    b1 = __ffma2_rn(make_float2(w.z, w.w), LB[2 * i4 + 1], b1);
+                }
+                if (cA < K) {
+                    sD[r0 * L.DS + cA] = __fadd_rn(a0.x, a0.y);
+                    if (r1 < nr) sD[r1 * L.DS + cA] = __fadd_rn(a1.x, a1.y);
+                }
+                if (cB < K) {
+                    sD[r0 * L.DS + cB] = __fadd_rn(b0.x, b0.y);
+                    if (r1 < nr) sD[r1 * L.DS + cB] = __fadd_rn(b1.x, b1.y);
+                }
+            }
+        }
+        // 4. the co-friend pair (x in F(v), y = v): the rows of F(v), the hub's first
+        //    K rows, against column K, in the same order
+        float cfd = 0.f;
+        const bool cf = A.ch == 0 && lane < K && ridA >= 0;
+        if (cf) {
+            const float4 *xr = sRow4 + lane * (MP / 4), *cv = sCol4 + K * (MP / 4);
+            float2 e = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i4 = 0; i4 < MP / 4; ++i4) {
+                const float4 xv = xr[i4], lw = cv[i4];
+                e = __ffma2_rn(make_float2(xv.x, xv.y), make_float2(lw.x, lw.y), e);
+                e = __ffma2_rn(make_float2(xv.z, xv.w), make_float2(lw.z, lw.w), e);
+            }
+            cfd = __fadd_rn(e.x, e.y);
+        }
+        __syncwarp();  // the dots are written, the row and column buffers read
+        // 5. the next item's copies: the buffers are free (its columns too, if it
+        //    starts a hub: this item's columns sit in registers)
+        const int slotB = (B.valid && B.ch == 0) ? slotA ^ 1 : slotA;
+        ridB = check_id(a, ridB, has_row(B, lane, 32));
+        if (B.valid) issue(B, ridB, B.ch == 0, slotB);
+        // 6. filter: lane t <-> row t of the item
+        unsigned mk = 0u;  // bit j: column j passed
+        int q = 0;
+        if (ridA >= 0) {  // rows past the item's end have no id
+            for (int j = 0; j < K; ++j) {
+                const float d = sD[lane * L.DS + j];
+                const int cj = cid[j];
+                const float thr = COL ? __fsub_rd(hcol[j], mA.phi) : mA.phi;
+                mk |= (d >= thr && cj >= 0 && cj != ridA) ? 1u << j : 0u;  // j <= 31
+            }
+            q = __popc(mk);
+            if (cf && cfd >= (COL ? __fsub_rd(hcol[K], mA.phi) : mA.phi)) {
+                sD[lane * L.DS + K] = cfd;  // the last survivor of the row
+                ++q;
+            }
+        }
+        // 7. reserve each row's bucket slots, then write the item's survivors
+        //    coalesced: lane t's entries follow those of lanes < t; entry k belongs
+        //    to the first lane whose inclusive prefix exceeds k
+        long long rowbase = -1;
+        if (q > 0) {
+            const int p = atomicAdd(&a.bcnt[ridA], q);
+            rowbase = mA.boff + p;
+            if (a.debug) {
+                const int64_t cap = (int64_t)K * K + (int64_t)(K + 1) * (a.cof_off[ridA + 1] - a.cof_off[ridA]);
+                if (p + q > cap) {
+                    atomicOr(a.err, kErrBucket);
+                    rowbase = -1;
+                }
+            }
+        }
+        sRB[lane] = rowbase;
+        sMask[lane] = mk;
+        int incl = q;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        sInc[lane] = incl;
+        __syncwarp();
+        for (int k = lane; k < total; k += 32) {
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int it = 0; it < 5; ++it) {
+                const int mid = (lo + hi) >> 1;
+                if (sInc[mid] > k) hi = mid;
+                else lo = mid + 1;
+            }
+            const int t = lo;
+            const int qq = k - (t ? sInc[t - 1] : 0);
+            const long long rb = sRB[t];
+            if (rb >= 0) {
+                // survivor qq of row t: its qq-th passing column, or (past them) the hub itself
+                const unsigned m = sMask[t];
+                const bool colj = qq < __popc(m);
+                const int j = colj ? (int)__fns(m, 0, qq + 1) : K;
+                const float d = sD[t * L.DS + j];
+                const int y = colj ? cid[j] : (int)A.v;
+                a.bent[rb + qq] =
+                    make_int2((int)sortable_bits(COL ? __fmul_rn(a.col_scale, __fsub_rn(hcol[j], d)) : -d), y);
+            }
+        }
+        __syncwarp();
+        // 8. advance
+        A = B;
+        ridA = ridB;
+        slotA = slotB;
+    }
+}
+
 // ------------------------------------------------------------------ host side
 
 namespace {
@@ -664,6 +947,24 @@ cudaError_t run_tma(knnd_handle *h, const TmaJoinArgs &a)
     return cudaGetLastError();
 }
 
+template <int MP, bool COL>
+cudaError_t run_wide(knnd_handle *h, const TmaJoinArgs &a)
+{
+    const int threads = 128;
+    const WideLayout L(MP, h->K, COL);
+    const size_t smem = (size_t)L.bytes * (threads / 32);
+    auto kern = join_wide_kernel<MP, COL>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    if (h->join_blocks > 0) per_sm = std::min(per_sm, h->join_blocks);
+    const int64_t need = (a.h_hi - a.h_lo + threads / 32 - 1) / (threads / 32);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)h->num_sms * per_sm));
+    kern<<<(unsigned)grid, threads, smem, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // Points below which the tuning table's choice of the TMA join is not followed
@@ -676,8 +977,10 @@ constexpr int64_t kTmaMinPoints = 65536;
 bool tma_join_supported(const knnd_handle *h)
 {
     if (h->prm.join_form != KNND_JOIN_TMA && h->n < kTmaMinPoints) return false;
+    // MP <= 32: join_tma_kernel; 48..72: join_wide_kernel (no bound audit: debug runs the plain join)
+    const bool shape = h->MP <= 32 || ((h->MP == 48 || h->MP == 64 || h->MP == 72) && !h->prm.debug);
     return h->prec != KNND_PREC_FP64 && h->round_flag == nullptr && h->prm.comparator != KNND_CMP_INNER &&
-           h->K <= 32 && h->MP <= 32 && encode_fn() != nullptr;
+           h->K <= 32 && shape && encode_fn() != nullptr;
 }
 
 cudaError_t launch_join_tma(knnd_handle *h, const int32_t *idx, int64_t h_lo, int64_t h_hi, int phase,
@@ -719,12 +1022,16 @@ cudaError_t launch_join_tma(knnd_handle *h, const int32_t *idx, int64_t h_lo, in
     const bool col = cmp == KNND_CMP_KL_REVERSE || cmp == KNND_CMP_SQEUCLIDEAN;
     // one row per lane: two rows per lane (R = 2: 64-row items, 162 registers, 17.4 KB of shared
     // memory per warp, 12 resident warps per SM) measured 4.05 against 3.10 ms per launch at
-    // n = 1e6, d = 20, K = 20
+    // n = 1e6, d = 20, K = 20, and 3.70 against 2.88 ms with 16 resident warps (the survivor
+    // dots kept in the row staging buffer, the next rows gathered after the output)
     switch (h->MP) {
     case 8: return col ? run_tma<8, true, 1>(h, a) : run_tma<8, false, 1>(h, a);
     case 16: return col ? run_tma<16, true, 1>(h, a) : run_tma<16, false, 1>(h, a);
     case 24: return col ? run_tma<24, true, 1>(h, a) : run_tma<24, false, 1>(h, a);
     case 32: return col ? run_tma<32, true, 1>(h, a) : run_tma<32, false, 1>(h, a);
+    case 48: return col ? run_wide<48, true>(h, a) : run_wide<48, false>(h, a);
+    case 64: return col ? run_wide<64, true>(h, a) : run_wide<64, false>(h, a);
+    case 72: return col ? run_wide<72, true>(h, a) : run_wide<72, false>(h, a);
     default: return cudaErrorInvalidValue;
     }
 }

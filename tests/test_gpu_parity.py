@@ -206,7 +206,7 @@ def test_incremental_proposals_same_graph(knnd, n, m, K):
             h = _handle(knnd, n, m, K, dtype="f32", precision="mixed_tma")
             c = h.build(pts, seed)
             h.close()
-            assert c["join_kernel"] == ("tma" if m < 32 and K <= 32 else "plain"), prec  # TMA: m + 1 <= 32
+            assert c["join_kernel"] == "tma", prec
             assert c["updates"] == b["updates"], prec
             assert torch.equal(c["idx"], b["idx"]) and torch.equal(c["key"], b["key"]), prec
 
@@ -461,3 +461,24 @@ def test_tuning_choices_batched_same_graphs(knnd):
     for x, y in zip(a, b):
         assert x["rounds"] == y["rounds"] and x["updates"] == y["updates"]
         assert torch.equal(x["idx"], y["idx"]) and torch.equal(x["key"], y["key"])
+
+
+@pytest.mark.parametrize("comparator", ["kl", "kl_reverse", "sqeuclidean"])
+@pytest.mark.parametrize("n,m,K", [(20_000, 41, 16), (20_000, 60, 32), (30_000, 65, 20), (9_000, 70, 7),
+                                   (5_001, 47, 31)])
+def test_wide_tma_join_equals_fp64(knnd, comparator, n, m, K):
+    # the TMA join of 41..72 coordinates (48, 64 or 72 padded; two columns per lane)
+    # gives the FP64 form's graph bit for bit under every comparator, ragged item
+    # tails and odd K included
+    seed = 43
+    pts = _gauss(n, m, seed, np.float32) if comparator == "sqeuclidean" else dirichlet_points(n, m, seed, np.float32)
+    pts = _dev(pts)
+    out = {}
+    for prec in ("fp64", "mixed_tma"):
+        h = _handle(knnd, n, m, K, dtype="f32", precision=prec, comparator=comparator)
+        out[prec] = h.build(pts, seed)
+        h.close()
+    a, b = out["fp64"], out["mixed_tma"]
+    assert b["join_kernel"] == "tma"
+    assert a["rounds"] == b["rounds"] and a["updates"] == b["updates"] and a["fcc_hits"] == b["fcc_hits"]
+    assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["key"], b["key"])
