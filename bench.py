@@ -46,6 +46,10 @@ WORKLOADS = {
     # the paper's largest Table 3 run (Sec. 4.4: 9-simplex, n = 2e6, K = 16)
     "n2e6_d9_K16": (2_000_000, 10, 16, 3, "KL K-NN descent build to the statistical stop, n=2e6 Dirichlet(1) points, "
                                           "d=9 (10 FP32 coords), K=16, seed 3 (Table 3 shape)"),
+    # profiling-size case of the n = 4e6, d = 64, K = 32 shape: both FP32 tables
+    # (n x 288 B each) still exceed the 129 MB L2, while the device holds about 6 GB
+    "n3e5_d64_K32": (300_000, 65, 32, 2, "KL K-NN descent build to the statistical stop, n=3e5 Dirichlet(1) points, "
+                                         "d=64 (65 FP32 coords), K=32, seed 2 (profiling size)"),
     # profiling-size case of the benchmark shape: the join's gather set (n x 208 B)
     # still exceeds the 129 MB L2, while the device holds about 6 GB
     "n8e5_d20_K20": (800_000, 21, 20, 1, "KL K-NN descent build to the statistical stop, n=8e5 Dirichlet(1) points, "
@@ -355,7 +359,7 @@ def gpu_single(args, name, rank, world, local, barrier):
 
     fma = fma_peaks(local) if not args.no_peaks else None
     clocks = Clocks(local)
-    mixed = run_form(args.form, args.steps, args.warmup, clocks)
+    mixed = run_form(args.form, args.steps, args.warmup, clocks, join_form=args.join_form)
     fp64 = run_form("fp64", args.fp64_steps, 1) if args.fp64_steps > 0 else None
     # the same build with incremental proposals (same graph, fewer candidates), one step
     incr = run_form(args.form, 1, 1, incremental=True) if args.steps > 0 else None
@@ -445,6 +449,8 @@ def gpu_single(args, name, rank, world, local, barrier):
                    "form": ("mixed: FP32 CUDA-core join filter + FP64 re-score (graph == FP64 form)"
                             if args.form == "mixed" else
                             "mixed: BF16 hi/lo x3 tcgen05 join tiles, FP32 accumulate + FP64 re-score (graph == FP64 form)"),
+                   "join_gathers": {"auto": "the tuning table's choice", "tma": "TMA (forced)",
+                                    "plain": "plain loads (forced)"}[args.join_form],
                    "proposals": "every pair the hub tiles meet (the paper's full pool)",
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -731,6 +737,8 @@ def main():
                     help="skip the n=4e6 d=64 K=32 and 4096-instance summary legs of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FMA pipe measurement")
+    ap.add_argument("--join-form", default="auto", choices=["auto", "tma", "plain"],
+                    help="the FP32 join's gathers for the timed builds (auto: the tuning table's choice)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
