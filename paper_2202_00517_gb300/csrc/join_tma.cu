@@ -615,9 +615,9 @@ __global__ void __launch_bounds__(128, R == 2 ? 3 : (MP <= 24 ? 5 : 4))
 // join_wide_kernel: the same filter for 41..72 real coordinates (MP 48, 64 or
 // 72; K <= 32).  One row per lane would hold MP coordinates in registers and
 // read every column coordinate once for one row.  Here, as in join_mixed_kernel
-// (join.cu), lane (g, p) holds the log rows of columns 2p and 2p + 1 in
-// registers and reads each coordinate of rows 2g + 2Gi and 2g + 2Gi + 1 (G row
-// groups) once for both columns: half the shared-memory reads per fma at these
+// (join.cu), lane (g, p) holds the log rows of two columns in registers and
+// reads each coordinate of rows 2g + 2Gi and 2g + 2Gi + 1 (G row groups) once
+// for both columns: half the shared-memory reads per fma at these
 // widths.  What the TMA adds to that layout: an item's 32 rows and a hub's K + 1
 // columns reach shared memory by tile::gather4, so the load/store pipe carries
 // no gathered sectors, and the next item's copies (its rows; for a new hub also
@@ -675,11 +675,13 @@ __global__ void __launch_bounds__(128, 2) join_wide_kernel(const __grid_constant
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     __syncwarp();
-    // scoring roles: lane (g, p) = columns 2p, 2p + 1 of row group g
+    // scoring roles: lane (g, p) = columns p and p + npairs of row group g (the
+    // columns 288 bytes apart at MP = 72: consecutive columns spread over four bank
+    // groups, so that reading them into registers conflicts 4-way, not 8-way)
     const int npairs = (K + 1) >> 1, G = 32 / npairs;
     const int g = lane / npairs, pr = lane - g * npairs;
     const bool active = g < G;
-    const int cA = 2 * pr, cB = 2 * pr + 1;
+    const int cA = pr, cB = pr + npairs;
 
     HubWalk walk;
     walk.c0 = walk.c1 = 0;
