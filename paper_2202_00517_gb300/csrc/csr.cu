@@ -71,9 +71,9 @@ __device__ __forceinline__ bool friend_of(const int32_t *__restrict__ f, int K, 
 // F(x)) stands twice among the hub's rows, F(v) followed by coF(v), and its
 // second row proposes exactly the pairs (x, y), y in F(v), of its first; the
 // pool of Sec. 3.1 is a set, so the copy adds nothing.  Such arcs are counted
-// in deg_mut and placed at the end of coF(v), the others in deg at its front:
-// the TMA join reads the first deg[v] entries, every other consumer the whole
-// list (the same set of pairs either way).
+// in deg_mut and placed at the end of coF(v) (slot -1 - k: the k-th from the
+// end), the others in deg at its front: the TMA joins read the first deg[v]
+// entries, every other consumer the whole list (the same set of pairs).
 __global__ void csr_count_kernel(const int32_t *__restrict__ idx, const double *__restrict__ key, int64_t n, int K,
                                  int32_t *__restrict__ deg, int32_t *__restrict__ slot, double *__restrict__ tau,
                                  int32_t *__restrict__ idxK,
