@@ -105,8 +105,9 @@ typedef struct {
                                      what fits) */
     int32_t join_form;            /* KNND_JOIN_TMA or KNND_JOIN_PLAIN: how the FP32 filter gathers its rows
                                      (0: the tuning table's, TMA only from n >= 65536 on); the TMA form
-                                     needs up to 32 padded coordinates, K <= 32, no incremental proposals
-                                     and not the inner product, else plain loads are used */
+                                     needs m <= 72 (padded to 8, 16, 24, 32, 48, 64 or 72 coordinates),
+                                     K <= 32, no incremental proposals, not the inner product and, past
+                                     32 padded coordinates, debug = 0; else plain loads are used */
 } knnd_params;
 
 /* The join kernel a build ran (knnd_build_info.join_kernel); the first two are
