@@ -138,9 +138,9 @@ def code_sha256(path):
     return hashlib.sha256(re.sub(r"\s+", "", text).encode()).hexdigest()
 
 
-def join_traffic_per_launch(name, source="join.cu", profile_prefix="join_mixed"):
-    """DRAM bytes per join launch from the committed ncu summary of the workload,
-    if it was taken on the current join code (the summary records the source's
+def profile_figure(name, source, profile_prefix, label):
+    """The figure `label: value` of the committed ncu summary of the workload, if the
+    summary was taken on the current join code (it records the source's
     code_sha256); else None."""
     src = os.path.join(ROOT, "paper_2202_00517_gb300", "csrc", source)
     prof = os.path.join(ROOT, "profiles", f"{profile_prefix}_{name}.md")
@@ -148,10 +148,28 @@ def join_traffic_per_launch(name, source="join.cu", profile_prefix="join_mixed")
         return None
     text = open(prof).read()
     m_sha = re.search(re.escape(source) + r" code sha256:\s*([0-9a-f]{64})", text)
-    m_b = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", text)
+    m_b = re.search(re.escape(label) + r":\s*([0-9.eE+]+)", text)
     if not (m_sha and m_b) or m_sha.group(1) != code_sha256(src):
         return None
     return float(m_b.group(1))
+
+
+def join_traffic_per_launch(name, source="join.cu", profile_prefix="join_mixed"):
+    """DRAM bytes per join launch from the committed ncu summary (see profile_figure)."""
+    return profile_figure(name, source, profile_prefix, "dram bytes per full-size launch")
+
+
+def join_l1_view(name, source, profile_prefix, launch_s, sm_mhz, sms):
+    """The join against its L1 data pipe: the ncu wavefronts per full-size launch of
+    the committed summary over this run's launch time, per SM and cycle, against the
+    pipe's one 128-byte wavefront per SM per cycle; None without a current summary."""
+    w = profile_figure(name, source, profile_prefix, "l1 data-pipe wavefronts per full-size launch")
+    if w is None or launch_s <= 0 or not sm_mhz:
+        return None
+    achieved = w / (launch_s * sm_mhz * 1e6 * sms)
+    return {"wavefronts_per_launch": w, "achieved": achieved, "peak": 1.0, "unit": "wavefronts per SM per cycle",
+            "frac": achieved, "sm_mhz": sm_mhz,
+            "peak_source": "ncu l1tex__data_pipe_lsu_wavefronts.sum.peak_sustained (152 per cycle, 1 per SM)"}
 
 
 FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz
@@ -440,6 +458,11 @@ def gpu_single(args, name, rank, world, local, barrier):
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6800 GB/s",
                      "traffic_over_compulsory": traffic / compulsory if traffic else None}}
+    if tma:
+        clk = mixed.get("clocks") or {}
+        roofline["l1_view"] = join_l1_view(name, "join_tma.cu", "join_tma", join_avg_s,
+                                           clk.get("sm_mhz") or 2070.0,
+                                           torch.cuda.get_device_properties(dev).multi_processor_count)
     total_ph = max(1e-9, sum(st["phase_ms"].values()))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,

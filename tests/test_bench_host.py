@@ -77,3 +77,25 @@ def test_evaluation_count():
     # n K initial keys plus n (K + 2 K^2) proposals per round (Sec. 4.4 footnote)
     assert bench.evals_of(10, 2, 0) == 20
     assert bench.evals_of(10, 2, 3) == 20 + 3 * 10 * (2 + 8)
+
+
+def test_l1_view_from_the_profiled_source(tmp_path, monkeypatch):
+    # the L1 view divides the summary's wavefronts per launch by the run's launch time,
+    # per SM and cycle, and is left out once the join code has changed
+    src = tmp_path / "paper_2202_00517_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (src / "join_tma.cu").write_text("int f() { return 1; }\n")
+    sha = bench.code_sha256(str(src / "join_tma.cu"))
+    (tmp_path / "profiles" / "join_tma_w.md").write_text(
+        f"join_tma.cu code sha256: {sha}\n\nl1 data-pipe wavefronts per full-size launch: 3.0e+08\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    v = bench.join_l1_view("w", "join_tma.cu", "join_tma", 1e-3, 2000.0, 150)
+    assert abs(v["achieved"] - 3.0e8 / (1e-3 * 2000e6 * 150)) < 1e-12 and v["peak"] == 1.0
+    (src / "join_tma.cu").write_text("int f() { return 2; }\n")
+    assert bench.join_l1_view("w", "join_tma.cu", "join_tma", 1e-3, 2000.0, 150) is None
+
+
+def test_committed_profile_gives_the_l1_view():
+    v = bench.join_l1_view("n1e6_d20_K20", "join_tma.cu", "join_tma", 2.9e-3, 2070.0, 152)
+    assert v is None or 0.3 < v["achieved"] < 1.1
