@@ -474,7 +474,9 @@ def gpu_single(args, name, rank, world, local, barrier):
                             "mixed: BF16 hi/lo x3 tcgen05 join tiles, FP32 accumulate + FP64 re-score (graph == FP64 form)"),
                    "join_gathers": {"auto": "the tuning table's choice", "tma": "TMA (forced)",
                                     "plain": "plain loads (forced)"}[args.join_form],
-                   "proposals": "every pair the hub tiles meet (the paper's full pool)",
+                   "proposals": ("evals count the paper's pool multiset, n(K + 2K^2) pairs a round; the TMA "
+                                 "join skips, from round 2, the repeated pairs of co-friends that are also "
+                                 "friends of the hub"),
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "build_s_mixed": mixed_ms / steps / 1e3,
